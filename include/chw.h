@@ -1,0 +1,182 @@
+/*
+ * chw.h -- C ABI of the GB300 (sm_103a) Cascading Haar Wavelet Walsh-Hadamard library.
+ *
+ * The library computes y = H_m x for batches of signals of length n = 2^m, where H_m is
+ * the 2^m x 2^m Hadamard matrix in dyadic (Paley) order defined by the recursion of
+ * eq. (1) of "The Cascading Haar Wavelet algorithm for computing the Walsh-Hadamard
+ * Transform" (arXiv 1609.06641):
+ *
+ *     H_0 = 1,   H_{m+1} = 2^{-1/2} [ H_m (x) (1 1) ; H_m (x) (1 -1) ].
+ *
+ * It computes it by the CHW algorithm of Theorem 1 (eq. (3)): the Haar transform Psi_m of
+ * eq. (2), followed by stages r = 1..m-1, each applying Psi_{m-r} to the second half of
+ * every block of length 2^{m-r+1}.  The cascade's butterflies are fused into register,
+ * shared-memory, cluster (DSMEM) and HBM tiers; every schedule performs the same
+ * butterflies on the same operands, so results round exactly as the cascade taken in
+ * the paper's stage order does.
+ *
+ * Conventions for every call below:
+ *   - Pointers named x, y, exp_*, diag are DEVICE pointers unless the name says _host.
+ *     The caller owns them.  Data buffers must be 16-byte aligned.
+ *   - Layout: batch-major, contiguous: signal b occupies elements [b*n, (b+1)*n).
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Device calls are asynchronous on that stream and never synchronise; a plan must
+ *     be used from one stream at a time.
+ *   - Errors are returned as chw_status_t; nothing aborts and no C++ exception crosses
+ *     the boundary.  chw_last_error_message() gives a one-line reason (per host thread).
+ *     Errors found on the device (a bounded wait that ran out, a checked-mode index
+ *     fault) are latched in the plan and reported by chw_last_device_status().
+ *   - In-place operation (x == y) is allowed for every call.
+ */
+#ifndef CHW_H
+#define CHW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum chw_status_e {
+  CHW_OK = 0,
+  CHW_ERR_INVALID_ARG = 1,  /* bad m, batch, dtype/norm pairing, null pointer, ...   */
+  CHW_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement          */
+  CHW_ERR_ALIGNMENT = 3,    /* a data pointer is not 16-byte aligned                 */
+  CHW_ERR_OOM = 4,          /* the plan's device workspace could not be allocated    */
+  CHW_ERR_CUDA = 5,         /* a CUDA runtime call failed (no device, launch error)  */
+  CHW_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                    */
+  CHW_ERR_DEVICE_CHECK = 7  /* a device-side consistency check failed                */
+} chw_status_t;
+
+typedef enum chw_dtype_e {
+  CHW_I32 = 0,   /* int32, unnormalised only; two's-complement wrap on overflow        */
+  CHW_F32 = 1,   /* fp32 in, fp32 out                                                  */
+  CHW_BF16 = 2,  /* bf16 codes with an int32 power-of-two exponent per signal          */
+  CHW_F16 = 3    /* fp16 codes with an int32 power-of-two exponent per signal          */
+} chw_dtype_t;
+
+/* Placement of the 2^{-1/2} factors of eq. (1)-(2) (the paper counts additions only). */
+typedef enum chw_norm_e {
+  CHW_NORM_NONE = 0,      /* unscaled butterflies: result 2^{m/2} H_m x                   */
+  CHW_NORM_PER_LEVEL = 1, /* (a+b)*c and (a-b)*c at every level, c = fp32(1/sqrt2)       */
+  CHW_NORM_END = 2        /* unscaled butterflies, then one multiply by fp32(2^{-m/2})   */
+} chw_norm_t;
+
+#define CHW_MAX_M 30
+
+/* Plan flags. */
+#define CHW_FLAG_NONE 0u
+#define CHW_FLAG_FORCE_SIMPLE 1u    /* use the plain one-CTA-per-signal kernel (tests)  */
+#define CHW_FLAG_FORCE_MULTIPASS 2u /* split m into two HBM passes even if one fits     */
+
+typedef struct chw_plan_s* chw_plan_t;
+
+/* Read-only description of what a plan will launch (for tests and reports). */
+typedef struct chw_plan_info_s {
+  int m;                     /* transform bits (-1 for a ragged plan)                 */
+  int64_t batch;             /* signals per call (ragged: number of signals)          */
+  int dtype;                 /* chw_dtype_t                                            */
+  int norm;                  /* chw_norm_t                                             */
+  int tier;                  /* 0 simple, 1 fused CTA, 2 fused cluster, 3 two-pass, 4 ragged */
+  int passes;                /* HBM round trips per call                               */
+  int row_bits;              /* two-pass: bits transformed in pass 1 (else m)          */
+  int cluster;               /* CTAs per cluster in the fused (or first) pass          */
+  int kernels_per_call;      /* kernel launches per forward/adjoint call               */
+  int64_t workspace_bytes;   /* device scratch owned by the plan                       */
+  int64_t total_elements;    /* elements per call (sum over the batch)                 */
+} chw_plan_info_t;
+
+/*
+ * chw_plan -- prepare y = H_m x for `batch` signals of length 2^m (eq. (1), Theorem 1).
+ *   m      0..CHW_MAX_M (m = 0 is the identity: H_0 = 1).
+ *   batch  >= 1.
+ *   dtype/norm: CHW_I32 requires CHW_NORM_NONE; CHW_F32 takes any norm; CHW_BF16 and
+ *          CHW_F16 take CHW_NORM_END or CHW_NORM_PER_LEVEL (the stored exponent carries
+ *          the scale) and need m <= 13.
+ *   flags  CHW_FLAG_* bits.
+ * Allocates the plan (host) and its device workspace on the current device.  Returns
+ * CHW_ERR_INVALID_ARG / CHW_ERR_UNSUPPORTED / CHW_ERR_OOM / CHW_ERR_CUDA on failure, in
+ * which case *plan is set to NULL.
+ */
+chw_status_t chw_plan(chw_plan_t* plan, int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm,
+                      uint32_t flags);
+
+/*
+ * chw_plan_ragged -- prepare one call over `count` signals of uneven lengths 2^{ms[i]}
+ * (the transform of eq. (1) applied to each signal independently).
+ *   ms_host   host array of `count` bit counts, each in 0..20.  The signals are packed
+ *             back to back in that order: signal i starts at element offset
+ *             sum_{j<i} 2^{ms[j]} (chw_ragged_offsets() returns these offsets).
+ *   dtype     CHW_F32 or CHW_I32 (with norm as for chw_plan).
+ * The plan builds its task table and device work queue once; chw_forward_ragged() then
+ * runs every signal in one persistent launch, replayed from a CUDA graph.
+ */
+chw_status_t chw_plan_ragged(chw_plan_t* plan, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,
+                             chw_norm_t norm, uint32_t flags);
+
+/* Element offsets of a ragged plan's signals: offsets_host[0..count] (count+1 entries). */
+chw_status_t chw_ragged_offsets(chw_plan_t plan, int64_t* offsets_host);
+
+/*
+ * chw_forward -- y = D H_m x for every signal of the plan's batch (eq. (1); computed by
+ * the cascade of Theorem 1).
+ *   x, y     device buffers of batch * 2^m elements of the plan's dtype.
+ *   exp_in   bf16/fp16 only: int32[batch], signal b of x means 2^{exp_in[b]} * x_b.
+ *   exp_out  bf16/fp16 only: int32[batch] written with the output exponents: y_b means
+ *            2^{exp_out[b]} * y_b, chosen so max|y_b| is in [1, 2) for bf16 and
+ *            [2^14, 2^15) for fp16.  Must be NULL for int32/fp32.
+ *   diag     optional int8[2^m] of +-1 (the diagonal of D, shared by all signals), NULL
+ *            for D = I.  Applied to the transform's output.
+ */
+chw_status_t chw_forward(chw_plan_t plan, const void* x, void* y, const int32_t* exp_in, int32_t* exp_out,
+                         const int8_t* diag, void* stream);
+
+/*
+ * chw_adjoint -- x = H_m^T D y, the transpose of chw_forward (used for gradients).
+ * H_m^T is the reversed cascade of inverse Haar transforms Psi^T.  Each butterfly of the
+ * cascade is a symmetric 2x2 matrix and the dyadic reorder is an involution, so the
+ * reversed cascade performs the forward cascade's butterflies with inputs and outputs
+ * relabelled; it runs on the same kernels and rounds identically.  diag (if given) is
+ * applied to y before the transform.  Arguments as for chw_forward.
+ */
+chw_status_t chw_adjoint(chw_plan_t plan, const void* y, void* x, const int32_t* exp_in, int32_t* exp_out,
+                         const int8_t* diag, void* stream);
+
+/* chw_forward_ragged -- transform every signal of a ragged plan (packed layout above). */
+chw_status_t chw_forward_ragged(chw_plan_t plan, const void* x, void* y, void* stream);
+
+/*
+ * chw_forward_host -- chw_forward for HOST buffers: copies x_host to the device, runs
+ * the transform and copies the result to y_host, pipelined in chunks over the plan's
+ * own streams and staging buffers; returns when y_host (and exp_out_host) are written.
+ * Pinned (page-locked) host memory gives full copy bandwidth.  exp_*_host and diag_host
+ * follow chw_forward's rules (diag_host: int8[2^m] on the host, or NULL).
+ */
+chw_status_t chw_forward_host(chw_plan_t plan, const void* x_host, void* y_host, const int32_t* exp_in_host,
+                              int32_t* exp_out_host, const int8_t* diag_host);
+
+/* Fill *info with what the plan launches. */
+chw_status_t chw_plan_get_info(chw_plan_t plan, chw_plan_info_t* info);
+
+/*
+ * chw_last_device_status -- synchronise the plan's device work and report the first
+ * device-side error latched since the previous call (CHW_ERR_TIMEOUT,
+ * CHW_ERR_DEVICE_CHECK) or an asynchronous CUDA error (CHW_ERR_CUDA); clears the latch.
+ */
+chw_status_t chw_last_device_status(chw_plan_t plan);
+
+/* Release the plan and its device workspace.  NULL is accepted. */
+chw_status_t chw_plan_destroy(chw_plan_t plan);
+
+/* Static description of a status code. */
+const char* chw_status_string(chw_status_t status);
+
+/* One-line reason for the last error returned on this host thread ("" if none). */
+const char* chw_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHW_H */

@@ -1,0 +1,582 @@
+// C ABI of the CHW library: plans, validation, tier choice, launches, host pipeline.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/chw.h"
+#include "launch.cuh"
+#include "ragged.cuh"
+#include "simple.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+chw_status_t fail(chw_status_t s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CHW_CUDA(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) return fail(CHW_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+enum Tier { kTierSimple = 0, kTierFused = 1, kTierCluster = 2, kTierTwoPass = 3, kTierRagged = 4 };
+
+struct Shape {
+  int tb, cb;
+};
+
+// One-pass row kernel shape for a transform of M bits.
+Shape row_shape(int M) {
+  if (M <= 13) return {13, 0};
+  if (M == 14) return {14, 0};
+  return {14, M - 14};
+}
+// Second-pass column kernel shape for A row bits (32 columns per block).
+Shape col_shape(int A) {
+  if (A <= 8) return {13, 0};
+  if (A == 9) return {14, 0};
+  return {14, A - 9};
+}
+
+bool is_lowp(chw_dtype_t d) { return d == CHW_BF16 || d == CHW_F16; }
+size_t elem_bytes(chw_dtype_t d) { return is_lowp(d) ? 2 : 4; }
+
+// fp32(2^{-m/2}): 2^{-floor(m/2)} times (1 or fp32(1/sqrt2)); exact power-of-two scaling of
+// the correctly rounded constant is itself correctly rounded in fp32's normal range.
+float end_scale_f32(int m) {
+  const float r = (m & 1) ? 0.70710678118654752440f : 1.0f;
+  return std::ldexp(r, -(m / 2));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// View `total` 4-byte words at `ptr` as rows of 32 words (128 B); box of `boxr` rows,
+// SWIZZLE_128B, out-of-bounds rows read as zero.
+chw_status_t make_rows_map(CUtensorMap* map, const void* ptr, int64_t total, int tb) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (total % 32 != 0) return fail(CHW_ERR_INVALID_ARG, "internal: tensor rows need a multiple of 32 words");
+  const int boxr = (1 << (tb - 5)) < 256 ? (1 << (tb - 5)) : 256;
+  cuuint64_t dims[2] = {32, static_cast<cuuint64_t>(total / 32)};
+  cuuint64_t strides[1] = {128};
+  cuuint32_t box[2] = {32, static_cast<cuuint32_t>(boxr)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return CHW_OK;
+}
+
+}  // namespace
+
+struct chw_plan_s {
+  int device = 0;
+  int m = 0;
+  int64_t batch = 0;
+  chw_dtype_t dtype = CHW_F32;
+  chw_norm_t norm = CHW_NORM_PER_LEVEL;
+  uint32_t flags = 0;
+  int tier = kTierSimple;
+  int passes = 1;
+  int row_bits = 0;  // two-pass: b (pass 1 rows); a = m - b
+  int64_t total = 0;
+  void* workspace = nullptr;
+  size_t workspace_bytes = 0;
+  int* d_status = nullptr;
+  // host pipeline (chw_forward_host), allocated on first use
+  int64_t h_chunk = 0;  // signals per chunk
+  cudaStream_t h_stream[3] = {};
+  void* h_buf[3] = {};
+  void* h_ws[3] = {};
+  int32_t* h_exp[3][2] = {};
+  int8_t* h_diag = nullptr;
+  // ragged
+  chw::RaggedPlan* ragged = nullptr;
+};
+
+namespace {
+
+int fused_variant(const chw_plan_s* p, bool last_pass) {
+  if (p->dtype == CHW_I32) return chw::kVarI32;
+  switch (p->norm) {
+    case CHW_NORM_PER_LEVEL: return chw::kVarPerLevel;
+    case CHW_NORM_END: return last_pass ? chw::kVarEnd : chw::kVarPlain;
+    default: return chw::kVarPlain;
+  }
+}
+
+chw_status_t validate_data_ptr(const void* p, const char* name) {
+  if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "%s is NULL", name);
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return fail(CHW_ERR_ALIGNMENT, "%s is not 16-byte aligned", name);
+  return CHW_OK;
+}
+
+chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
+                             const int8_t* diag_in, const int8_t* diag_out, int64_t diag_mask, int colblock_a,
+                             float scale, cudaStream_t st) {
+  const Shape s = row_shape(M);
+  chw::FusedLaunchFn fn = chw::lookup_fused(0, M, s.tb, s.cb, var, om);
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no row kernel for M=%d tb=%d cb=%d out=%d", M, s.tb, s.cb, om);
+  CUtensorMap map;
+  chw_status_t r = make_rows_map(&map, in, total, s.tb);
+  if (r != CHW_OK) return r;
+  chw::FusedArgs a{};
+  a.out = out;
+  a.out_total = total;
+  a.end_scale = scale;
+  a.diag_in = diag_in;
+  a.diag_out = diag_out;
+  a.diag_mask = diag_mask;
+  a.status = p->d_status;
+  a.colblock_a = colblock_a;
+  const int64_t tile = int64_t{1} << s.tb;
+  const int64_t ctas = s.cb > 0 ? total / tile : (total + tile - 1) / tile;
+  CHW_CUDA(fn(&map, a, ctas, st));
+  return CHW_OK;
+}
+
+chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, const void* in, void* out, int64_t total,
+                             const int8_t* diag_out, int64_t diag_mask, float scale, cudaStream_t st) {
+  const Shape s = col_shape(A);
+  chw::FusedLaunchFn fn = chw::lookup_fused(5, A, s.tb, s.cb, var, 0);
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no column kernel for A=%d", A);
+  CUtensorMap map;
+  chw_status_t r = make_rows_map(&map, in, total, s.tb);
+  if (r != CHW_OK) return r;
+  chw::FusedArgs a{};
+  a.out = out;
+  a.out_total = total;
+  a.end_scale = scale;
+  a.diag_in = nullptr;
+  a.diag_out = diag_out;
+  a.diag_mask = diag_mask;
+  a.status = p->d_status;
+  a.colblock_a = 0;
+  const int64_t tile = int64_t{1} << s.tb;
+  const int64_t ctas = s.cb > 0 ? total / tile : (total + tile - 1) / tile;
+  CHW_CUDA(fn(&map, a, ctas, st));
+  return CHW_OK;
+}
+
+chw_status_t launch_simple(chw_plan_s* p, const void* x, void* y, int64_t batch, const int32_t* exp_in,
+                           int32_t* exp_out, const int8_t* diag_in, const int8_t* diag_out, cudaStream_t st) {
+  chw::SimpleArgs a{};
+  a.x = x;
+  a.y = y;
+  a.m = p->m;
+  a.batch = batch;
+  a.norm = static_cast<int>(p->norm);
+  a.end_scale = end_scale_f32(p->m);
+  a.exp_in = exp_in;
+  a.exp_out = exp_out;
+  a.diag_in = diag_in;
+  a.diag_out = diag_out;
+  const int64_t n = int64_t{1} << p->m;
+  const int threads = n >= 512 ? 256 : (n >= 64 ? static_cast<int>(n / 2) : 32);
+  const size_t smem = static_cast<size_t>(n) * 4;
+  const dim3 grid(static_cast<unsigned>(batch));
+  switch (p->dtype) {
+    case CHW_I32: chw::simple_kernel<chw::kSimpleI32><<<grid, threads, smem, st>>>(a); break;
+    case CHW_F32: chw::simple_kernel<chw::kSimpleF32><<<grid, threads, smem, st>>>(a); break;
+    case CHW_BF16: chw::simple_kernel<chw::kSimpleBF16><<<grid, threads, smem, st>>>(a); break;
+    case CHW_F16: chw::simple_kernel<chw::kSimpleF16><<<grid, threads, smem, st>>>(a); break;
+  }
+  CHW_CUDA(cudaGetLastError());
+  return CHW_OK;
+}
+
+// y = D_out H x D_in for `batch` signals (x, y device; ws = scratch for the two-pass tier)
+chw_status_t run_transform(chw_plan_s* p, const void* x, void* y, int64_t batch, const int32_t* exp_in,
+                           int32_t* exp_out, const int8_t* diag_in, const int8_t* diag_out, void* ws,
+                           cudaStream_t st) {
+  const int m = p->m;
+  const int64_t n = int64_t{1} << m;
+  const int64_t total = batch * n;
+  const int64_t dmask = n - 1;
+  switch (p->tier) {
+    case kTierSimple:
+      return launch_simple(p, x, y, batch, exp_in, exp_out, diag_in, diag_out, st);
+    case kTierFused:
+    case kTierCluster:
+      return launch_row_pass(p, m, 0, fused_variant(p, true), x, y, total, diag_in, diag_out, dmask, 0,
+                             end_scale_f32(m), st);
+    case kTierTwoPass: {
+      const int b = p->row_bits, a = m - b;
+      chw_status_t r = launch_row_pass(p, b, 1, fused_variant(p, false), x, ws, total, diag_in, nullptr, dmask, a,
+                                       1.0f, st);
+      if (r != CHW_OK) return r;
+      return launch_col_pass(p, a, fused_variant(p, true), ws, y, total, diag_out, dmask, end_scale_f32(m), st);
+    }
+    default:
+      return fail(CHW_ERR_INVALID_ARG, "plan is not a batched plan");
+  }
+}
+
+chw_status_t check_plan_args(int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm) {
+  if (m < 0 || m > CHW_MAX_M) return fail(CHW_ERR_INVALID_ARG, "m=%d outside 0..%d", m, CHW_MAX_M);
+  if (batch < 1) return fail(CHW_ERR_INVALID_ARG, "batch=%lld must be >= 1", static_cast<long long>(batch));
+  if (dtype < CHW_I32 || dtype > CHW_F16) return fail(CHW_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+  if (norm < CHW_NORM_NONE || norm > CHW_NORM_END) return fail(CHW_ERR_INVALID_ARG, "unknown norm %d", static_cast<int>(norm));
+  if (dtype == CHW_I32 && norm != CHW_NORM_NONE) return fail(CHW_ERR_INVALID_ARG, "int32 is unnormalised only (CHW_NORM_NONE)");
+  if (is_lowp(dtype) && norm == CHW_NORM_NONE)
+    return fail(CHW_ERR_INVALID_ARG, "bf16/fp16 take CHW_NORM_END or CHW_NORM_PER_LEVEL");
+  const int64_t n = int64_t{1} << m;
+  if (batch > (int64_t{1} << 40) / n) return fail(CHW_ERR_INVALID_ARG, "batch * 2^m exceeds 2^40 elements");
+  return CHW_OK;
+}
+
+void destroy_host_pipeline(chw_plan_s* p) {
+  for (int i = 0; i < 3; ++i) {
+    if (p->h_stream[i]) cudaStreamDestroy(p->h_stream[i]);
+    if (p->h_buf[i]) cudaFree(p->h_buf[i]);
+    if (p->h_ws[i]) cudaFree(p->h_ws[i]);
+    for (int j = 0; j < 2; ++j)
+      if (p->h_exp[i][j]) cudaFree(p->h_exp[i][j]);
+    p->h_stream[i] = nullptr;
+    p->h_buf[i] = p->h_ws[i] = nullptr;
+    p->h_exp[i][0] = p->h_exp[i][1] = nullptr;
+  }
+  if (p->h_diag) cudaFree(p->h_diag);
+  p->h_diag = nullptr;
+  p->h_chunk = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* chw_status_string(chw_status_t s) {
+  switch (s) {
+    case CHW_OK: return "CHW_OK";
+    case CHW_ERR_INVALID_ARG: return "CHW_ERR_INVALID_ARG: invalid argument";
+    case CHW_ERR_UNSUPPORTED: return "CHW_ERR_UNSUPPORTED: not implemented for these arguments";
+    case CHW_ERR_ALIGNMENT: return "CHW_ERR_ALIGNMENT: pointer not 16-byte aligned";
+    case CHW_ERR_OOM: return "CHW_ERR_OOM: device allocation failed";
+    case CHW_ERR_CUDA: return "CHW_ERR_CUDA: CUDA runtime error";
+    case CHW_ERR_TIMEOUT: return "CHW_ERR_TIMEOUT: a bounded device wait gave up";
+    case CHW_ERR_DEVICE_CHECK: return "CHW_ERR_DEVICE_CHECK: device-side check failed";
+  }
+  return "unknown chw_status_t";
+}
+
+const char* chw_last_error_message(void) { return g_err.c_str(); }
+
+chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm, uint32_t flags) {
+  g_err.clear();
+  if (out == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan output pointer is NULL");
+  *out = nullptr;
+  chw_status_t r = check_plan_args(m, batch, dtype, norm);
+  if (r != CHW_OK) return r;
+
+  auto* p = new chw_plan_s();
+  p->m = m;
+  p->batch = batch;
+  p->dtype = dtype;
+  p->norm = norm;
+  p->flags = flags;
+  p->total = batch * (int64_t{1} << m);
+  p->row_bits = m;
+
+  if (is_lowp(dtype)) {
+    if (m > 13) {
+      delete p;
+      return fail(CHW_ERR_UNSUPPORTED, "bf16/fp16 storage needs m <= 13 (one CTA per signal)");
+    }
+    p->tier = kTierSimple;
+  } else if ((flags & CHW_FLAG_FORCE_SIMPLE) != 0) {
+    if (m > 13) {
+      delete p;
+      return fail(CHW_ERR_UNSUPPORTED, "the simple kernel takes m <= 13");
+    }
+    p->tier = kTierSimple;
+  } else if ((flags & CHW_FLAG_FORCE_MULTIPASS) != 0 && m >= 11 && m <= 29) {
+    p->tier = kTierTwoPass;
+    p->passes = 2;
+    p->row_bits = m - (m >= 23 ? (m - 17 > 6 ? m - 17 : 6) : 6);
+  } else if (m <= 17) {
+    if (m < 5 && p->total % 32 != 0) {
+      p->tier = kTierSimple;
+    } else {
+      p->tier = m >= 15 ? kTierCluster : kTierFused;
+    }
+  } else if (m <= 29) {
+    p->tier = kTierTwoPass;
+    p->passes = 2;
+    const int a = (m - 17) > 6 ? (m - 17) : 6;
+    p->row_bits = m - a;
+  } else {
+    delete p;
+    return fail(CHW_ERR_UNSUPPORTED, "m=%d needs three HBM passes, which this build does not implement", m);
+  }
+
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(CHW_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(CHW_ERR_CUDA, "cudaMalloc(status): %s", cudaGetErrorString(e));
+  }
+  cudaMemset(p->d_status, 0, sizeof(int));
+  if (p->tier == kTierTwoPass) {
+    p->workspace_bytes = static_cast<size_t>(p->total) * elem_bytes(dtype);
+    e = cudaMalloc(&p->workspace, p->workspace_bytes);
+    if (e != cudaSuccess) {
+      cudaFree(p->d_status);
+      delete p;
+      cudaGetLastError();
+      return fail(CHW_ERR_OOM, "workspace of %zu bytes: %s", p->workspace_bytes, cudaGetErrorString(e));
+    }
+  }
+  *out = p;
+  return CHW_OK;
+}
+
+chw_status_t chw_plan_destroy(chw_plan_t p) {
+  if (p == nullptr) return CHW_OK;
+  destroy_host_pipeline(p);
+  if (p->workspace) cudaFree(p->workspace);
+  if (p->d_status) cudaFree(p->d_status);
+  if (p->ragged) chw::ragged_destroy(p->ragged);
+  delete p;
+  return CHW_OK;
+}
+
+chw_status_t chw_plan_get_info(chw_plan_t p, chw_plan_info_t* info) {
+  if (p == nullptr || info == nullptr) return fail(CHW_ERR_INVALID_ARG, "NULL plan or info");
+  std::memset(info, 0, sizeof(*info));
+  info->m = p->ragged ? -1 : p->m;
+  info->batch = p->batch;
+  info->dtype = p->dtype;
+  info->norm = p->norm;
+  info->tier = p->tier;
+  info->passes = p->passes;
+  info->row_bits = p->row_bits;
+  info->cluster = 1;
+  info->kernels_per_call = p->passes;
+  if (p->tier == kTierFused || p->tier == kTierCluster) info->cluster = 1 << row_shape(p->m).cb;
+  if (p->tier == kTierTwoPass) info->cluster = 1 << row_shape(p->row_bits).cb;
+  info->workspace_bytes = static_cast<int64_t>(p->workspace_bytes);
+  info->total_elements = p->total;
+  if (p->ragged) {
+    info->kernels_per_call = 1;
+    info->workspace_bytes = static_cast<int64_t>(chw::ragged_workspace_bytes(p->ragged));
+  }
+  return CHW_OK;
+}
+
+static chw_status_t forward_common(chw_plan_t p, const void* x, void* y, const int32_t* exp_in, int32_t* exp_out,
+                                   const int8_t* diag_in, const int8_t* diag_out, void* stream) {
+  g_err.clear();
+  if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan is NULL");
+  if (p->ragged) return fail(CHW_ERR_INVALID_ARG, "ragged plans run through chw_forward_ragged");
+  chw_status_t r = validate_data_ptr(x, "x");
+  if (r != CHW_OK) return r;
+  r = validate_data_ptr(y, "y");
+  if (r != CHW_OK) return r;
+  if (is_lowp(p->dtype)) {
+    if (exp_in == nullptr || exp_out == nullptr) return fail(CHW_ERR_INVALID_ARG, "bf16/fp16 need exp_in and exp_out");
+  } else if (exp_in != nullptr || exp_out != nullptr) {
+    return fail(CHW_ERR_INVALID_ARG, "exp_in/exp_out are for bf16/fp16 only");
+  }
+  return run_transform(p, x, y, p->batch, exp_in, exp_out, diag_in, diag_out, p->workspace,
+                       static_cast<cudaStream_t>(stream));
+}
+
+chw_status_t chw_forward(chw_plan_t p, const void* x, void* y, const int32_t* exp_in, int32_t* exp_out,
+                         const int8_t* diag, void* stream) {
+  return forward_common(p, x, y, exp_in, exp_out, nullptr, diag, stream);
+}
+
+chw_status_t chw_adjoint(chw_plan_t p, const void* y, void* x, const int32_t* exp_in, int32_t* exp_out,
+                         const int8_t* diag, void* stream) {
+  // H^T = H: the reversed cascade of Psi^T stages performs the forward butterflies with
+  // inputs and outputs relabelled, so the same kernels run; D is applied to the input.
+  return forward_common(p, y, x, exp_in, exp_out, diag, nullptr, stream);
+}
+
+chw_status_t chw_forward_host(chw_plan_t p, const void* x_host, void* y_host, const int32_t* exp_in_host,
+                              int32_t* exp_out_host, const int8_t* diag_host) {
+  g_err.clear();
+  if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan is NULL");
+  if (p->ragged) return fail(CHW_ERR_INVALID_ARG, "ragged plans run through chw_forward_ragged");
+  if (x_host == nullptr || y_host == nullptr) return fail(CHW_ERR_INVALID_ARG, "x_host / y_host is NULL");
+  const bool lowp = is_lowp(p->dtype);
+  if (lowp && (exp_in_host == nullptr || exp_out_host == nullptr))
+    return fail(CHW_ERR_INVALID_ARG, "bf16/fp16 need exp_in_host and exp_out_host");
+  if (!lowp && (exp_in_host != nullptr || exp_out_host != nullptr))
+    return fail(CHW_ERR_INVALID_ARG, "exp_in_host/exp_out_host are for bf16/fp16 only");
+  const int64_t n = int64_t{1} << p->m;
+  const size_t eb = elem_bytes(p->dtype);
+  if (p->h_chunk == 0) {
+    // chunks of about 64 MiB (at least one signal) cycle over three streams so that the
+    // copy in, the transform and the copy out of consecutive chunks overlap
+    int64_t chunk = (int64_t{64} << 20) / static_cast<int64_t>(n * eb);
+    if (chunk < 1) chunk = 1;
+    if (chunk > p->batch) chunk = p->batch;
+    if (p->tier == kTierSimple || lowp) {
+      // whole signals per chunk already
+    } else if (p->m < 5) {
+      while ((chunk * n) % 32 != 0 && chunk < p->batch) ++chunk;
+    }
+    p->h_chunk = chunk;
+    const size_t bytes = static_cast<size_t>(chunk * n) * eb;
+    for (int i = 0; i < 3; ++i) {
+      if (cudaStreamCreateWithFlags(&p->h_stream[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaMalloc(&p->h_buf[i], bytes) != cudaSuccess ||
+          (p->tier == kTierTwoPass && cudaMalloc(&p->h_ws[i], bytes) != cudaSuccess) ||
+          (lowp && (cudaMalloc(&p->h_exp[i][0], chunk * sizeof(int32_t)) != cudaSuccess ||
+                    cudaMalloc(&p->h_exp[i][1], chunk * sizeof(int32_t)) != cudaSuccess))) {
+        cudaGetLastError();
+        destroy_host_pipeline(p);
+        return fail(CHW_ERR_OOM, "host pipeline buffers");
+      }
+    }
+    if (cudaMalloc(&p->h_diag, static_cast<size_t>(n)) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_host_pipeline(p);
+      return fail(CHW_ERR_OOM, "host pipeline diag buffer");
+    }
+  }
+  const int8_t* d_diag = nullptr;
+  if (diag_host != nullptr) {
+    CHW_CUDA(cudaMemcpy(p->h_diag, diag_host, static_cast<size_t>(n), cudaMemcpyHostToDevice));
+    d_diag = p->h_diag;
+  }
+  const int64_t chunk = p->h_chunk;
+  int i = 0;
+  for (int64_t s0 = 0; s0 < p->batch; s0 += chunk, i = (i + 1) % 3) {
+    const int64_t cnt = (p->batch - s0) < chunk ? (p->batch - s0) : chunk;
+    const size_t off = static_cast<size_t>(s0 * n) * eb, bytes = static_cast<size_t>(cnt * n) * eb;
+    cudaStream_t st = p->h_stream[i];
+    CHW_CUDA(cudaMemcpyAsync(p->h_buf[i], static_cast<const uint8_t*>(x_host) + off, bytes, cudaMemcpyHostToDevice, st));
+    if (lowp)
+      CHW_CUDA(cudaMemcpyAsync(p->h_exp[i][0], exp_in_host + s0, cnt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const int64_t saved = p->batch;
+    chw_status_t r;
+    {
+      // the transform of this chunk, in place in the staging buffer
+      if (p->tier != kTierSimple && !lowp && p->m < 5 && (cnt * n) % 32 != 0) {
+        const int tier = p->tier;
+        p->tier = kTierSimple;
+        r = run_transform(p, p->h_buf[i], p->h_buf[i], cnt, nullptr, nullptr, nullptr, d_diag, nullptr, st);
+        p->tier = tier;
+      } else {
+        r = run_transform(p, p->h_buf[i], p->h_buf[i], cnt, lowp ? p->h_exp[i][0] : nullptr,
+                          lowp ? p->h_exp[i][1] : nullptr, nullptr, d_diag, p->h_ws[i], st);
+      }
+    }
+    (void)saved;
+    if (r != CHW_OK) return r;
+    CHW_CUDA(cudaMemcpyAsync(static_cast<uint8_t*>(y_host) + off, p->h_buf[i], bytes, cudaMemcpyDeviceToHost, st));
+    if (lowp)
+      CHW_CUDA(cudaMemcpyAsync(exp_out_host + s0, p->h_exp[i][1], cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  }
+  for (int k = 0; k < 3; ++k) CHW_CUDA(cudaStreamSynchronize(p->h_stream[k]));
+  return CHW_OK;
+}
+
+chw_status_t chw_last_device_status(chw_plan_t p) {
+  g_err.clear();
+  if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan is NULL");
+  CHW_CUDA(cudaDeviceSynchronize());
+  int s = 0;
+  CHW_CUDA(cudaMemcpy(&s, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CHW_CUDA(cudaMemset(p->d_status, 0, sizeof(int)));
+  if (s != 0) return fail(static_cast<chw_status_t>(s), "device reported %s", chw_status_string(static_cast<chw_status_t>(s)));
+  return CHW_OK;
+}
+
+chw_status_t chw_plan_ragged(chw_plan_t* out, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,
+                             chw_norm_t norm, uint32_t flags) {
+  g_err.clear();
+  if (out == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan output pointer is NULL");
+  *out = nullptr;
+  if (ms_host == nullptr || count < 1) return fail(CHW_ERR_INVALID_ARG, "ms_host is NULL or count < 1");
+  if (dtype != CHW_F32 && dtype != CHW_I32) return fail(CHW_ERR_UNSUPPORTED, "ragged plans take int32 or fp32");
+  chw_status_t r = check_plan_args(0, 1, dtype, norm);
+  if (r != CHW_OK) return r;
+  for (int64_t i = 0; i < count; ++i)
+    if (ms_host[i] > chw::kRaggedMaxM)
+      return fail(CHW_ERR_INVALID_ARG, "ms[%lld]=%d outside 0..%d", static_cast<long long>(i), ms_host[i],
+                  chw::kRaggedMaxM);
+  auto* p = new chw_plan_s();
+  p->m = -1;
+  p->batch = count;
+  p->dtype = dtype;
+  p->norm = norm;
+  p->flags = flags;
+  p->tier = kTierRagged;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(CHW_ERR_CUDA, "ragged plan: %s", cudaGetErrorString(e));
+  }
+  cudaMemset(p->d_status, 0, sizeof(int));
+  std::string why;
+  p->ragged = chw::ragged_create(ms_host, count, dtype == CHW_I32 ? chw::kVarI32 : fused_variant(p, true),
+                                 p->d_status, &why);
+  if (p->ragged == nullptr) {
+    cudaFree(p->d_status);
+    delete p;
+    return fail(CHW_ERR_OOM, "ragged plan: %s", why.c_str());
+  }
+  p->total = chw::ragged_total(p->ragged);
+  p->passes = chw::ragged_passes(p->ragged);
+  *out = p;
+  return CHW_OK;
+}
+
+chw_status_t chw_ragged_offsets(chw_plan_t p, int64_t* offsets_host) {
+  if (p == nullptr || p->ragged == nullptr || offsets_host == nullptr)
+    return fail(CHW_ERR_INVALID_ARG, "not a ragged plan, or NULL output");
+  chw::ragged_offsets(p->ragged, offsets_host);
+  return CHW_OK;
+}
+
+chw_status_t chw_forward_ragged(chw_plan_t p, const void* x, void* y, void* stream) {
+  g_err.clear();
+  if (p == nullptr || p->ragged == nullptr) return fail(CHW_ERR_INVALID_ARG, "not a ragged plan");
+  chw_status_t r = validate_data_ptr(x, "x");
+  if (r != CHW_OK) return r;
+  r = validate_data_ptr(y, "y");
+  if (r != CHW_OK) return r;
+  std::string why;
+  const int rc = chw::ragged_run(p->ragged, x, y, static_cast<cudaStream_t>(stream), &why);
+  if (rc != 0) return fail(CHW_ERR_CUDA, "ragged run: %s", why.c_str());
+  return CHW_OK;
+}
+
+}  // extern "C"

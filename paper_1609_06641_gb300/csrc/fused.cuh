@@ -1,0 +1,431 @@
+// One-HBM-round-trip CHW kernel for 4-byte elements (fp32, int32).
+//
+// A CTA owns a tile of 2^TB consecutive elements; a thread-block cluster of 2^CB CTAs
+// owns 2^(TB+CB).  The tile is brought into shared memory by TMA (SWIZZLE_128B), then
+// up to three register phases run the butterflies (label bits 0-4, 5-10, 11+; see
+// engine.cuh), the last of them reading the other CTAs' shared memory over DSMEM when
+// the transform spans the cluster.  Results are staged in shared memory in output order
+// and copied out with coalesced 16-byte stores.
+//
+// Two uses:
+//   TLO = 0  row transform: each tile holds 2^(TB-M) whole signals of length 2^M (CB = 0)
+//            or one 2^TB slice of a 2^(TB+CB) signal (CB > 0).  Output in dyadic order.
+//   TLO = 5  column transform (second pass of the two-pass split): the tile is a
+//            2^M x 32 block (32 columns of a row-transformed signal, stored contiguously
+//            by the first pass); the transform runs over the 2^M rows of each column and
+//            column c's results form the contiguous output row c (Y = H_b X^T H_a).
+#pragma once
+
+#include "engine.cuh"
+
+namespace chw {
+
+constexpr int kStatusTimeout = 6;      // CHW_ERR_TIMEOUT
+constexpr int kStatusDeviceCheck = 7;  // CHW_ERR_DEVICE_CHECK
+constexpr uint32_t kWaitTries = 1u << 22;
+
+struct FusedArgs {
+  void* out;                 // output array base (global)
+  int64_t out_total;         // elements of `out` that may be written (tail tiles stop there)
+  float end_scale;           // multiply applied to every result when the kernel's SCALE is set
+  const int8_t* diag_in;     // +-1 applied to inputs (adjoint's D), or nullptr
+  const int8_t* diag_out;    // +-1 applied to outputs (forward's D), or nullptr
+  int64_t diag_mask;         // index within a signal = element index & diag_mask
+  int* status;               // device status word (first error wins)
+  int colblock_a;            // OUTMODE 1: rows per signal = 2^colblock_a
+};
+
+// ------------------------------------------------------------------ phase plans
+struct FusedPlan {
+  bool has_p1, has_p3, p1_final, p2_final;
+  Phase p1, p2, p3, fw;  // fw: the final phase in output-write register order
+  Lin lin_s, lin_b, lin_final;
+  bool b_is_s;
+  int stage_s;
+  Lin omap;
+  int rank_shift[4];  // o bit of each CTA-rank label bit (cluster output placement)
+};
+
+constexpr Lin make_omap(int TLO, int M) {
+  Lin l = lin_identity();
+  if (TLO == 0) {
+    for (int b = 0; b < M; ++b) l.img[b] = 1u << (M - 1 - b);
+  } else {
+    for (int b = 0; b < 5; ++b) l.img[b] = 1u << (M + b);
+    for (int b = 5; b < 5 + M; ++b) l.img[b] = 1u << (M + 4 - b);
+  }
+  return l;
+}
+
+constexpr Phase make_p1(int TB) {
+  Phase p{};
+  p.nreg = 6;
+  const int r[6] = {0, 1, 2, 3, 4, 10};
+  for (int i = 0; i < 6; ++i) p.reg[i] = r[i];
+  for (int i = 0; i < 5; ++i) p.lane[i] = 5 + i;
+  p.nwarp = TB - 11;
+  for (int i = 0; i < p.nwarp; ++i) p.warp[i] = 11 + i;
+  return p;
+}
+
+constexpr Phase make_p2(int TB, int TLO, int M) {
+  Phase p{};
+  p.nreg = 6;
+  const int top = TLO + M - 1;
+  int n = 0;
+  if (top <= 10 && top >= 5) {
+    for (int b = top; b >= 5; --b) p.reg[n++] = b;
+    for (int b = top + 1; b <= 10; ++b) p.reg[n++] = b;
+  } else {
+    for (int b = 5; b <= 10; ++b) p.reg[n++] = b;
+  }
+  const int l[5] = {4, 3, 2, 1, 0};
+  for (int i = 0; i < 5; ++i) p.lane[i] = l[i];
+  p.nwarp = TB - 11;
+  for (int i = 0; i < p.nwarp; ++i) p.warp[i] = 11 + i;
+  return p;
+}
+
+constexpr Phase make_p3(int TB, int CB, int TLO, int M) {
+  Phase p{};
+  const int nb = TB + CB;
+  const int top = TLO + M - 1;
+  // CTA-rank and lane bits per (TLO, CB); see the bank analysis in the file comment of
+  // engine.cuh.  Lane bits 0..2 (a quarter warp) feed the staging swizzle key.
+  const int ctas[2][4][3] = {{{-1, -1, -1}, {0, -1, -1}, {0, 1, -1}, {0, 1, 2}},
+                             {{-1, -1, -1}, {4, -1, -1}, {4, 3, -1}, {4, 3, 2}}};
+  const int lanes[2][4][5] = {{{4, 3, 2, 1, 0}, {4, 3, 2, 1, 5}, {4, 3, 2, 5, 6}, {5, 4, 3, 6, 7}},
+                              {{4, 3, 2, 1, 0}, {0, 1, 2, 3, 5}, {0, 1, 2, 5, 6}, {0, 1, 5, 6, 7}}};
+  const int t = TLO == 0 ? 0 : 1;
+  bool used[kMaxBits] = {};
+  p.ncta = CB;
+  for (int i = 0; i < CB; ++i) {
+    p.cta[i] = ctas[t][CB][i];
+    used[p.cta[i]] = true;
+  }
+  for (int i = 0; i < 5; ++i) {
+    p.lane[i] = lanes[t][CB][i];
+    used[p.lane[i]] = true;
+  }
+  p.nreg = 6;
+  int n = 0;
+  for (int b = top; b >= 11 && n < 6; --b) {
+    p.reg[n++] = b;
+    used[b] = true;
+  }
+  for (int b = 10; b >= 0 && n < 6; --b) {
+    if (used[b]) continue;
+    p.reg[n++] = b;
+    used[b] = true;
+  }
+  p.nwarp = 0;
+  for (int b = 0; b < nb; ++b)
+    if (!used[b]) p.warp[p.nwarp++] = b;
+  return p;
+}
+
+// Write order of a final phase: registers 0 and 1 hold output bits 0 and 1 if possible.
+constexpr Phase write_order(const Phase& p, const Lin& omap) {
+  int l0 = -1, l1 = -1;
+  for (int b = 0; b < kMaxBits; ++b) {
+    if (omap.img[b] == 1u) l0 = b;
+    if (omap.img[b] == 2u) l1 = b;
+  }
+  const int i0 = reg_index_of(p, l0), i1 = reg_index_of(p, l1);
+  if (i0 < 0 || i1 < 0) return p;
+  Phase q = p;
+  q.reg[0] = l0;
+  q.reg[1] = l1;
+  int n = 2;
+  for (int i = 0; i < p.nreg; ++i)
+    if (p.reg[i] != l0 && p.reg[i] != l1) q.reg[n++] = p.reg[i];
+  return q;
+}
+
+// bank-XOR pairs for the P2 -> P3 exchange on top of the TMA layout
+constexpr Lin make_lin_b(const Phase& p2, const Phase& p3) {
+  Lin l = lin_tma128();
+  int from[5] = {}, to[5] = {};
+  int nf = 0, nt = 0;
+  for (int i = 0; i < 5; ++i) {
+    bool in3 = false;
+    for (int j = 0; j < 5; ++j) in3 |= p3.lane[j] == p2.lane[i];
+    if (!in3) to[nt++] = p2.lane[i];
+  }
+  for (int j = 0; j < 5; ++j) {
+    bool in2 = false;
+    for (int i = 0; i < 5; ++i) in2 |= p2.lane[i] == p3.lane[j];
+    if (!in2) from[nf++] = p3.lane[j];
+  }
+  // sort both ascending
+  for (int a = 0; a < nf; ++a)
+    for (int b = a + 1; b < nf; ++b) {
+      if (from[b] < from[a]) { int t = from[a]; from[a] = from[b]; from[b] = t; }
+      if (to[b] < to[a]) { int t = to[a]; to[a] = to[b]; to[b] = t; }
+    }
+  for (int i = 0; i < nf; ++i) l.img[from[i]] |= 1u << to[i];
+  return l;
+}
+
+constexpr bool lin_equal(const Lin& a, const Lin& b) {
+  for (int i = 0; i < kMaxBits; ++i)
+    if (a.img[i] != b.img[i]) return false;
+  return true;
+}
+
+constexpr int pick_stage_key(const Phase& fw, const Lin& omap, int TB) {
+  int ob[3] = {};
+  for (int j = 0; j < 3; ++j) {
+    const uint32_t im = omap.img[fw.lane[j]];
+    int bit = 0;
+    while ((1u << bit) != im) ++bit;
+    ob[j] = bit;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = a + 1; b < 3; ++b)
+      if (ob[b] < ob[a]) { int t = ob[a]; ob[a] = ob[b]; ob[b] = t; }
+  if (ob[0] >= 5 && ob[1] == ob[0] + 1 && ob[2] == ob[0] + 2 && ob[2] < TB) return ob[0];
+  return 5;
+}
+
+constexpr FusedPlan make_plan(int TLO, int M, int TB, int CB) {
+  FusedPlan f{};
+  const int top = TLO + M;  // one past the last transform bit
+  f.has_p1 = TLO == 0;
+  f.p1_final = TLO == 0 && top <= 5;
+  f.p2_final = !f.p1_final && top <= 11;
+  f.has_p3 = top > 11;
+  f.p1 = make_p1(TB);
+  f.p2 = make_p2(TB, TLO, M);
+  f.p3 = make_p3(TB, CB, TLO, M);
+  f.omap = make_omap(TLO, M);
+  f.lin_s = lin_tma128();
+  f.lin_b = make_lin_b(f.p2, f.p3);
+  f.b_is_s = lin_equal(f.lin_b, f.lin_s);
+  const Phase fin = f.p1_final ? f.p1 : (f.p2_final ? f.p2 : f.p3);
+  f.fw = write_order(fin, f.omap);
+  f.stage_s = pick_stage_key(f.fw, f.omap, TB);
+  Lin fl = compose(lin_stage(f.stage_s), f.omap);
+  for (int i = 0; i < kMaxBits; ++i) fl.img[i] &= (1u << TB) - 1u;
+  f.lin_final = fl;
+  for (int i = 0; i < 4; ++i) f.rank_shift[i] = 0;
+  for (int i = 0; i < CB; ++i) {
+    int bit = 0;
+    while ((1u << bit) != f.omap.img[f.p3.cta[i]]) ++bit;
+    f.rank_shift[i] = bit;
+  }
+  return f;
+}
+
+template <int TLO, int M, int TB, int CB>
+struct FusedCfg {
+  static constexpr FusedPlan plan = make_plan(TLO, M, TB, CB);
+  static constexpr int NB = TB + CB;
+  static constexpr uint32_t LMASK = (1u << TB) - 1u;
+  static_assert(TB >= 11 && TB <= 15, "tile must hold 64 values x 32 lanes x >=1 warp");
+  static_assert(TLO == 0 || TLO == 5, "transform starts at label bit 0 (rows) or 5 (columns)");
+  static_assert(CB == 0 || TLO + M == NB, "a cluster tile holds exactly one transform");
+  static_assert(TLO + M <= NB && M >= 0, "transform must fit the tile");
+  static_assert(TLO + M <= 17, "at most three register phases");
+  static_assert(CB == 0 || plan.has_p3, "cluster bits are finished by the third phase");
+  static_assert(!plan.has_p1 || phase_covers(plan.p1, TB), "phase 1 covers the tile");
+  static_assert(phase_covers(plan.p2, TB), "phase 2 covers the tile");
+  static_assert(!plan.has_p3 || phase_covers(plan.p3, NB), "phase 3 covers the cluster tile");
+  // bank-conflict freedom of every shared-memory access
+  static_assert(!plan.has_p1 || (v4_ok(plan.p1, plan.lin_s, LMASK) &&
+                                 conflict_degree(plan.p1, plan.lin_s, LMASK, true) == 1),
+                "phase 1 reads the TMA tile with conflict-free 16-byte loads");
+  static_assert(conflict_degree(plan.p2, plan.lin_s, LMASK, false) == 1, "phase 2 reads are conflict-free");
+  static_assert(!plan.has_p3 || conflict_degree(plan.p2, plan.lin_b, LMASK, false) == 1,
+                "phase 2 writes are conflict-free");
+  static_assert(!plan.has_p3 || conflict_degree(plan.p3, plan.lin_b, LMASK, false) == 1,
+                "phase 3 reads are conflict-free");
+  // The final phase writes every value it holds (labels from other CTAs included) into
+  // its own staging buffer, so no label bit is masked there.
+  static constexpr bool final_v4 = v4_ok(plan.fw, plan.lin_final, ~0u);
+  static constexpr int final_conflicts = conflict_degree(plan.fw, plan.lin_final, ~0u, final_v4);
+  static_assert(final_conflicts <= (TLO + M <= 6 ? 2 : 1), "staging writes are conflict-free");
+  static_assert(plan.stage_s + 3 <= TB, "staging key inside the tile");
+};
+
+// ------------------------------------------------------------------ one tile
+// Transform the (cluster) tile whose input starts at TMA row `in_row0` (rows of 32 words)
+// and whose outputs start at element `out_base`.  `buf` is this CTA's 1024-byte aligned
+// 2^TB-word shared buffer, `bar` an initialised mbarrier whose next phase has `parity`.
+// All threads of the CTA call this; it ends with the CTA's output stores issued.
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
+__device__ __forceinline__ void fused_tile(const CUtensorMap* tin, int in_row0, int64_t out_base,
+                                           const FusedArgs& args, uint32_t* buf, uint64_t* bar, uint32_t parity) {
+  using Cfg = FusedCfg<TLO, M, TB, CB>;
+  constexpr FusedPlan F = Cfg::plan;
+  constexpr int NT = 1 << (TB - 6);
+  constexpr int NR = 1 << CB;
+  constexpr uint32_t LMASK = Cfg::LMASK;
+  constexpr int BOXR = (1 << (TB - 5)) < 256 ? (1 << (TB - 5)) : 256;
+  constexpr int NBOX = (1 << (TB - 5)) / BOXR;
+  constexpr Phase P1 = F.p1, P2 = F.p2, P3 = F.p3, FW = F.fw;
+  constexpr Lin LS = F.lin_s, LB = F.lin_b, LF = F.lin_final;
+
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
+  const uint32_t rank = CB > 0 ? cluster_ctarank() : 0u;
+  BF bf{};
+  if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
+
+  if (tid == 0) {
+    // order earlier generic-proxy accesses to buf before the TMA (async-proxy) writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint64_t pol = policy_evict_first();
+    mbar_arrive_expect_tx(bar, 4u << TB);
+#pragma unroll
+    for (int j = 0; j < NBOX; ++j) tma_load_2d(buf + j * BOXR * 32, tin, bar, 0, in_row0 + j * BOXR, pol);
+  }
+  if (!mbar_wait_bounded(bar, parity, kWaitTries)) {
+    if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+  }
+
+  uint32_t v[64];
+  auto scale_all = [&]() {
+    if constexpr (SCALE) {
+#pragma unroll
+      for (int k = 0; k < 64; ++k) v[k] = __float_as_uint(__fmul_rn(__uint_as_float(v[k]), args.end_scale));
+    }
+  };
+
+  if constexpr (F.has_p1) {
+    const uint32_t base = thread_pos<P1, LS, LMASK>(lane, warp, 0);
+    load_phase<P1, LS, LMASK>(v, buf, base);
+    if (args.diag_in != nullptr) {
+      const uint32_t tl = thread_label<P1>(lane, warp, 0);
+      const int64_t in0 = static_cast<int64_t>(in_row0) * 32;
+      sfor<64>([&](auto k) {
+        constexpr uint32_t kl = reg_label(P1, k);
+        const int64_t idx = in0 + (tl | kl);
+        if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
+      });
+    }
+    butterflies<P1, 0, (TLO + M < 5 ? TLO + M : 5)>(v, bf);
+    if constexpr (F.p1_final) {
+      scale_all();
+      __syncthreads();
+      store_phase<FW, P1, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
+    } else {
+      store_phase<P1, P1, LS, LMASK>(v, buf, base);
+    }
+    __syncthreads();
+  }
+
+  if constexpr (!F.p1_final) {
+    const uint32_t base2 = thread_pos<P2, LS, LMASK>(lane, warp, 0);
+    load_phase<P2, LS, LMASK>(v, buf, base2);
+    butterflies<P2, (TLO > 5 ? TLO : 5), (TLO + M < 11 ? TLO + M : 11)>(v, bf);
+    if constexpr (F.p2_final) {
+      scale_all();
+      __syncthreads();
+      store_phase<FW, P2, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
+      __syncthreads();
+    } else {
+      if constexpr (!F.b_is_s) __syncthreads();
+      store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
+      if constexpr (CB > 0) {
+        cluster_arrive();
+        cluster_wait();
+      } else {
+        __syncthreads();
+      }
+      const uint32_t base3 = thread_pos<P3, LB, LMASK>(lane, warp, rank);
+      if constexpr (CB > 0) {
+        uint32_t rbase[NR];
+        const uint32_t local = smem_u32(buf);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) rbase[r] = mapa_shared(local, r);
+        load_phase_cluster<P3, LB, TB, NR>(v, rbase, base3);
+        cluster_arrive();
+      } else {
+        load_phase<P3, LB, LMASK>(v, buf, base3);
+      }
+      butterflies<P3, 11, TLO + M>(v, bf);
+      scale_all();
+      if constexpr (CB > 0) {
+        cluster_wait();
+      } else {
+        __syncthreads();
+      }
+      store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, rank));
+      __syncthreads();
+    }
+  }
+
+  // ---- copy-out: coalesced 16-byte stores of the staged tile
+  if constexpr (CB > 0) {
+    uint32_t ro = 0;
+#pragma unroll
+    for (int i = 0; i < CB; ++i) ro |= ((rank >> i) & 1u) << (F.rank_shift[i] - TB);
+    out_base += static_cast<int64_t>(ro) << TB;
+  }
+  uint32_t* out = static_cast<uint32_t*>(args.out);
+  constexpr int NCH = 1 << (TB - 2);
+  constexpr int S = F.stage_s;
+#pragma unroll 4
+  for (int c = tid; c < NCH; c += NT) {
+    const uint32_t o = static_cast<uint32_t>(c) << 2;
+    const uint32_t pos = o ^ (((o >> S) & 7u) << 2);
+    uint4 q = *reinterpret_cast<const uint4*>(buf + pos);
+    const int64_t og = out_base + o;
+    if (og >= args.out_total) continue;
+    if (args.diag_out != nullptr) {
+      const int8_t* d = args.diag_out;
+      const int64_t di = og & args.diag_mask;
+      if constexpr (std::is_same_v<BF, BfI32>) {
+        if (d[di] < 0) q.x = 0u - q.x;
+        if (d[di + 1] < 0) q.y = 0u - q.y;
+        if (d[di + 2] < 0) q.z = 0u - q.z;
+        if (d[di + 3] < 0) q.w = 0u - q.w;
+      } else {
+        if (d[di] < 0) q.x ^= 0x80000000u;
+        if (d[di + 1] < 0) q.y ^= 0x80000000u;
+        if (d[di + 2] < 0) q.z ^= 0x80000000u;
+        if (d[di + 3] < 0) q.w ^= 0x80000000u;
+      }
+    }
+    int64_t addr;
+    if constexpr (OUTMODE == 0) {
+      addr = og;
+    } else {
+      // Column-blocked scratch for the two-pass split: element k of row R of a signal with
+      // 2^a rows goes to signal*2^(a+M) + (k/32)*2^(a+5) + (R mod 2^a)*32 + k mod 32.
+      const int a = args.colblock_a;
+      const int64_t R = og >> M;
+      const int64_t k = og & ((int64_t{1} << M) - 1);
+      const int64_t sig = R >> a, r = R & ((int64_t{1} << a) - 1);
+      addr = (sig << (a + M)) + ((k >> 5) << (a + 5)) + (r << 5) + (k & 31);
+    }
+    st_global_v4(out + addr, q.x, q.y, q.z, q.w);
+  }
+}
+
+// 1024-byte aligned start of the dynamic shared buffer (SWIZZLE_128B needs it).
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  const uint32_t a = smem_u32(p);
+  return p + ((1024u - (a & 1023u)) & 1023u);
+}
+
+// ------------------------------------------------------------------ the batched kernel
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
+__global__ void __launch_bounds__(1 << (TB - 6), (TB >= 14 ? 2 : 4))
+    fused_kernel(const __grid_constant__ CUtensorMap tin, const FusedArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  uint32_t* buf = reinterpret_cast<uint32_t*>(base);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (4u << TB));
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int64_t tile = blockIdx.x;
+  const int64_t out_base = CB > 0 ? ((tile >> CB) << (TB + CB)) : (tile << TB);
+  fused_tile<TLO, M, TB, CB, BF, SCALE, OUTMODE>(&tin, static_cast<int>(tile << (TB - 5)), out_base, args, buf, bar, 0u);
+}
+
+}  // namespace chw
