@@ -11,6 +11,7 @@ Sources are hashed so an unchanged tree is not rebuilt.  Run as
 import concurrent.futures as cf
 import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -18,7 +19,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OBJ = os.path.join(HERE, "_build")
+OBJ = os.path.join(HERE, "_build", platform.machine())  # objects never cross architectures
 LIB = os.path.join(HERE, "libchw.so")
 STAMP = os.path.join(OBJ, "sources.sha256")
 
