@@ -1,0 +1,491 @@
+"""Benchmark of the CHW Walsh-Hadamard library on GB300: one JSON line on rank 0.
+
+Headline workload: y = H_16 x for 4096 fp32 signals of 65536 elements (dyadic order,
+normalised by one 2^-8 multiply), N(0,1) inputs.  One step is one chw_forward over the
+whole batch; the metric is effective HBM bandwidth, 2 * n * 4 bytes per signal (read x
+once, write y once) divided by the device time.  Inputs (1 GiB) exceed the 129 MB L2, so
+no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-extra]
+
+Under torchrun (N > 1) every rank transforms its own batch (independent signals, no
+collective on the data path: weak scaling); the step time is the maximum over ranks.
+``--impl reference`` times the CPU oracle (plain FP64 numpy) on bounded samples of the
+same workload instead.
+"""
+
+import argparse
+import ctypes
+import json
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "WHT effective HBM GB/s (% peak) at stated error; bf16/ragged vs plain fp32"
+M, BATCH, SEED = 16, 4096, 2
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------- helpers
+def gbs(nbytes, seconds):
+    return nbytes / seconds / 1e9
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value, world, device=None):
+    """Maximum of a float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+class ClockSampler:
+    """Samples SM clock, max clock, power and clock-event reasons through NVML (ctypes)."""
+
+    REASONS = {
+        0x1: "gpu_idle",
+        0x2: "applications_clocks_setting",
+        0x4: "sw_power_cap",
+        0x8: "hw_slowdown",
+        0x10: "sync_boost",
+        0x20: "sw_thermal_slowdown",
+        0x40: "hw_thermal_slowdown",
+        0x80: "hw_power_brake_slowdown",
+        0x100: "display_clock_setting",
+    }
+
+    def __init__(self, index, period=0.005):
+        self.samples = []
+        self.period = period
+        self.ok = False
+        self.max_mhz = None
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if self.nvml.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.h)) != 0:
+                return
+            mx = ctypes.c_uint()
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+            self.ok = True
+        except OSError:
+            self.ok = False
+
+    def _read(self):
+        clk, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk))
+        self.nvml.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(pw))
+        fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or getattr(
+            self.nvml, "nvmlDeviceGetCurrentClocksThrottleReasons"
+        )
+        fn(self.h, ctypes.byref(rs))
+        return clk.value, pw.value / 1000.0, rs.value
+
+    def start(self):
+        self.stop_flag = False
+        if not self.ok:
+            return
+
+        def run():
+            while not self.stop_flag:
+                self.samples.append(self._read())
+                time.sleep(self.period)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag = True
+        if self.ok:
+            self.thread.join()
+            self.samples.append(self._read())
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["nvml unavailable"]}
+        clk = np.array([s[0] for s in self.samples])
+        bits = 0
+        for s in self.samples:
+            bits |= s[2]
+        reasons = [name for b, name in self.REASONS.items() if bits & b]
+        return {
+            "sm_mhz": float(np.median(clk)),
+            "sm_max_mhz": self.max_mhz,
+            "reasons": reasons,
+            "samples": len(self.samples),
+            "power_w_max": float(max(s[1] for s in self.samples)),
+        }
+
+
+def time_device(fn, steps, warmup, world, stream, sampler=None):
+    """W untimed calls, then K calls bracketed by barrier + synchronize, CUDA events on `stream`."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.stop()
+    barrier(world)
+    return start.elapsed_time(end) / steps  # ms per step
+
+
+def traffic_from_profile(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this build."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kernel_key)
+    if not ent:
+        return None
+    from paper_1609_06641_gb300 import build
+
+    if ent.get("build_digest") != build._digest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_rate(m, rows, seconds_budget=10.0):
+    """Oracle (FP64 fast WHT + dyadic reorder) on `rows`; repeats until the budget; GB/s."""
+    import oracle
+
+    nbytes = 2 * rows.shape[0] * (1 << m) * 4
+    reps, t0 = 0, time.perf_counter()
+    ref = None
+    while True:
+        ref = oracle.wht_fast_dyadic(rows.astype(np.float64), m)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_budget:
+            break
+    return gbs(nbytes * reps, el), ref, reps, el
+
+
+def cpu_baseline_leg(x_rows, y_rows, budget):
+    import oracle
+
+    rate, ref, reps, el = oracle_rate(M, x_rows, budget)
+    err = float(oracle.rel_err_per_signal(y_rows, ref).max())
+    return (
+        {
+            "value": rate,
+            "unit": "GB/s",
+            "cores": 1,
+            "kind": "oracle",
+            "sample": f"{x_rows.shape[0]} of the {BATCH} signals (m={M}), FP64 numpy fast WHT + dyadic "
+            f"reorder, repeated {reps}x over {el:.1f} s; GB/s counts 2*n*4 bytes per signal",
+        },
+        err,
+    )
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    from paper_1609_06641_gb300 import workloads as W
+
+    sample = 16
+    rows = W.normal_f32(M, sample, SEED)
+    import oracle
+
+    for _ in range(args.warmup):
+        oracle.wht_fast_dyadic(rows.astype(np.float64), M)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.wht_fast_dyadic(rows.astype(np.float64), M)
+    el = time.perf_counter() - t0
+    nbytes = 2 * sample * (1 << M) * 4
+    value = gbs(nbytes * args.steps, el)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "GB/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic: N(0,1) fp32 signals, numpy PCG64 seed 2",
+        "config": workload_config(),
+        "cpu_baseline": {
+            "value": value,
+            "unit": "GB/s",
+            "cores": 1,
+            "kind": "oracle",
+            "sample": f"each step: {sample} signals of m={M} through the FP64 oracle (plain numpy, one core)",
+        },
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config():
+    return {
+        "workload": "y = H_16 x (dyadic order, CHW cascade), 4096 signals x 65536 fp32, normalised by one "
+        "fp32(2^-8) multiply; inputs 1 GiB > 129 MB L2, no flush between steps",
+        "m": M,
+        "batch": BATCH,
+        "norm": "end",
+        "algorithmic_bytes_per_step": 2 * BATCH * (1 << M) * 4,
+    }
+
+
+# ---------------------------------------------------------------- extra configurations
+def extra_measurements(chw, torch, dev, steps, warmup, peak):
+    """Device-timed throughput of the other benchmark shapes (inputs drawn on the device)."""
+    out = {}
+
+    def rec(name, nbytes, ms, launches, **kw):
+        v = gbs(nbytes, ms / 1e3)
+        out[name] = {"GB/s": round(v, 1), "frac_of_peak": round(v / peak, 4), "ms_per_call": round(ms, 4),
+                     "launches_per_call": launches, **kw}
+
+    st = torch.cuda.current_stream()
+    g = torch.Generator(device=dev).manual_seed(7)
+    k = max(3, steps // 2)
+    # fp32 per-level normalisation and int32 on the headline shape
+    x = torch.randn(BATCH, 1 << M, device=dev, generator=g)
+    y = torch.empty_like(x)
+    p = chw.chw_plan(M, BATCH, "f32", "per_level")
+    ms = time_device(lambda: chw.chw_forward(p, x, y), k, warmup, 1, st)
+    rec("m16_b4096_f32_per_level", 2 * x.numel() * 4, ms, 1)
+    xi = torch.randint(-(2**14), 2**14 + 1, (BATCH, 1 << M), device=dev, dtype=torch.int32, generator=g)
+    yi = torch.empty_like(xi)
+    pi = chw.chw_plan(M, BATCH, "i32", "none")
+    ms = time_device(lambda: chw.chw_forward(pi, xi, yi), k, warmup, 1, st)
+    rec("m16_b4096_i32", 2 * xi.numel() * 4, ms, 1)
+    del xi, yi
+    # long signals: two HBM passes
+    for m, b in ((26, 4), (28, 1)):
+        xl = torch.rand(b, 1 << m, device=dev, generator=g) * 2 - 1
+        yl = torch.empty_like(xl)
+        pl = chw.chw_plan(m, b, "f32", "end")
+        ms = time_device(lambda: chw.chw_forward(pl, xl, yl), k, warmup, 1, st)
+        rec(f"m{m}_b{b}_f32_two_pass", 2 * xl.numel() * 4, ms, 2,
+            dram_pass_frac=round(gbs(4 * xl.numel() * 4, ms / 1e3) / peak, 4))
+        del xl, yl, pl
+    # 16-bit storage, m = 12, batch 16384
+    for fmt, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        xq = (torch.randn(16384, 1 << 12, device=dev, generator=g)).to(tdt)
+        yq = torch.empty_like(xq)
+        ei = torch.zeros(16384, dtype=torch.int32, device=dev)
+        eo = torch.empty_like(ei)
+        pq = chw.chw_plan(12, 16384, fmt, "end")
+        ms = time_device(lambda: chw.chw_forward(pq, xq, yq, ei, eo), k, warmup, 1, st)
+        rec(f"m12_b16384_{fmt}", 2 * xq.numel() * 2, ms, 1)
+        del xq, yq
+    # D H_m layer, m = 14, batch 512: forward and adjoint
+    xd = torch.randn(512, 1 << 14, device=dev, generator=g)
+    yd = torch.empty_like(xd)
+    d = (1 - 2 * torch.randint(0, 2, (1 << 14,), device=dev, generator=g)).to(torch.int8)
+    pd = chw.chw_plan(14, 512, "f32", "end")
+    ms = time_device(lambda: chw.chw_forward(pd, xd, yd, diag=d), k, warmup, 1, st)
+    rec("m14_b512_DH_forward", 2 * xd.numel() * 4, ms, 1)
+    ms = time_device(lambda: chw.chw_adjoint(pd, yd, xd, diag=d), k, warmup, 1, st)
+    rec("m14_b512_DH_adjoint", 2 * xd.numel() * 4, ms, 1)
+    del xd, yd
+    # ragged: 10,000 signals with m uniform on 6..20 (seed 5), one graph launch
+    from paper_1609_06641_gb300 import workloads as W
+
+    ms_arr, _ = W.ragged_ms(10000, 5)
+    pr = chw.chw_plan_ragged(ms_arr, "f32", "end")
+    total = int(chw.chw_plan_get_info(pr).total_elements)
+    xr = torch.randn(total, device=dev, generator=g)
+    yr = torch.empty_like(xr)
+    ms = time_device(lambda: chw.chw_forward_ragged(pr, xr, yr), k, warmup, 1, st)
+    useful = int(sum(1 << int(m) for m in ms_arr))
+    rec("ragged_10000_m6to20_f32", 2 * useful * 4, ms, 1, elements=useful)
+    return out
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="chw", choices=["chw", "reference"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--quick", action="store_true", help="device timing only (profiling runs)")
+    ap.add_argument("--m", type=int, default=M, help="transform bits of the timed workload")
+    ap.add_argument("--batch", type=int, default=BATCH, help="signals of the timed workload")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("gloo")
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
+
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1609_06641_gb300 as chw
+    from paper_1609_06641_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    peak, peak_kind = load_peaks()
+
+    m, batch = args.m, args.batch
+    x_host = W.normal_f32(m, batch, SEED + rank)  # each rank its own signals
+    x = torch.from_numpy(x_host).to(dev)
+    y = torch.empty_like(x)
+    plan = chw.chw_plan(m, batch, "f32", "end")
+    info = chw.chw_plan_get_info(plan)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    ms = time_device(lambda: chw.chw_forward(plan, x, y), args.steps, args.warmup, world, stream, sampler)
+    ms_max = max_over_ranks(ms, world, dev)
+    step_bytes = 2 * batch * (1 << m) * 4
+    value = world * gbs(step_bytes, ms_max / 1e3)
+    assert chw.chw_last_device_status(plan) == 0
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"m": m, "batch": batch, "ms_per_step": ms_max, "GB/s": value,
+                              "frac": value / world / peak, "clocks": sampler.summary()}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # end to end through the host-buffer entry point (pinned memory, copies inside)
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    chw.chw_forward_host(plan, xh, yh)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        chw.chw_forward_host(plan, xh, yh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    if not torch.equal(yh, y.cpu()):
+        raise RuntimeError("host-buffer path disagrees with the device path")
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    per_launch_ms = ms / info.kernels_per_call
+    achieved = gbs(step_bytes / info.kernels_per_call, per_launch_ms / 1e3)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: N(0,1) fp32 signals (numpy PCG64 seed 2 + rank), resident in HBM",
+        "config": workload_config(),
+        "pct_of_peak": round(100 * value / world / peak, 2),
+        "signals_per_s": round(world * BATCH / (ms_max / 1e3), 1),
+        "roofline": {
+            "bound": "hbm",
+            "achieved": round(achieved, 1),
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": traffic_from_profile("fused_m16_cluster4_end"),
+            "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "kernel": "fused_kernel<TLO=0,M=16,TB=14,CB=2> (4-CTA cluster per signal)",
+        },
+        "e2e": {
+            "value": round(gbs(step_bytes, e2e_s) * world, 1),
+            "unit": "GB/s",
+            "h2d_bytes_per_step": BATCH * (1 << M) * 4,
+            "d2h_bytes_per_step": BATCH * (1 << M) * 4,
+            "ms_per_step": round(e2e_s * 1e3, 3),
+            "api": "chw_forward_host (pinned host buffers, 64 MiB chunks over 3 streams)",
+        },
+        "gpu_launches": args.steps * info.kernels_per_call,
+        "clocks": sampler.summary(),
+    }
+    if world == 1:
+        rows = np.random.default_rng(0).choice(BATCH, 16, replace=False)
+        y_rows = y.cpu().numpy()[rows]
+        cpu, err = cpu_baseline_leg(x_host[rows], y_rows, args.cpu_budget)
+        line["cpu_baseline"] = cpu
+        line["error"] = {"max_rel_err_vs_fp64_oracle": err, "signals_checked": len(rows), "gate": 1e-6}
+        if not args.no_extra:
+            line["extra"] = extra_measurements(chw, torch, dev, args.steps, args.warmup, peak)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,67 @@
+"""Multi-rank host logic of bench.py on CPU: gloo, world size 2 (no GPU).
+
+Each rank transforms its own signals (weak scaling, no collective on the data path); the
+step time reported is the maximum over ranks and the value counts every rank's bytes.
+"""
+
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import os, sys
+sys.path.insert(0, {root!r})
+import torch.distributed as dist
+import bench
+dist.init_process_group("gloo")
+world, rank, local = bench.dist_env()
+local_ms = 1.0 + rank          # rank 1 is the slower one
+mx = bench.max_over_ranks(local_ms, world)
+bench.barrier(world)
+value = world * bench.gbs(1e9, mx / 1e3)
+print(f"RANK{{rank}} max={{mx}} value={{value}}", flush=True)
+dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def test_max_over_ranks_gloo_world2(tmp_path):
+    script = tmp_path / "child.py"
+    script.write_text(CHILD.format(root=ROOT))
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE="2", RANK=str(rank),
+                   LOCAL_RANK=str(rank))
+        procs.append(subprocess.Popen([sys.executable, str(script)], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.STDOUT, text=True))
+    outs = [p.communicate(timeout=120)[0] for p in procs]
+    for p, o in zip(procs, outs):
+        assert p.returncode == 0, o
+    for rank, o in enumerate(outs):
+        assert f"RANK{rank} max=2.0" in o, o
+        # 2 ranks x 1e9 bytes in the slowest rank's 2 ms
+        assert "value=1000.0" in o, o
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    import json
+
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"

@@ -1,0 +1,100 @@
+"""Ragged batches: one persistent, graph-replayed launch over signals of uneven length (GPU)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import assert_bitwise
+from paper_1609_06641_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def chw(cuda_device):
+    import paper_1609_06641_gb300 as chw
+    from paper_1609_06641_gb300 import build
+
+    build.build()
+    return chw
+
+
+def run(chw, ms, x, dtype="f32", norm="end", inplace=False, repeats=1):
+    import torch
+
+    p = chw.chw_plan_ragged(ms, dtype, norm)
+    off = chw.chw_ragged_offsets(p)
+    assert np.array_equal(off, W.ragged_offsets(ms))
+    xd = torch.from_numpy(x).cuda()
+    yd = xd if inplace else torch.empty_like(xd)
+    for _ in range(repeats):
+        if inplace:
+            xd.copy_(torch.from_numpy(x))
+        chw.chw_forward_ragged(p, xd, yd)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(p) == 0
+    return yd.cpu().numpy(), off, p
+
+
+def per_signal_ref(ms, off, x, dtype, norm):
+    outs = []
+    for i, m in enumerate(ms):
+        seg = x[off[i]: off[i] + (1 << int(m))][None, :]
+        outs.append(O.chw_cascade(seg, int(m), dtype, norm)[0])
+    return outs
+
+
+@pytest.mark.parametrize("norm", ["end", "per_level"])
+def test_ragged_mixed_lengths(chw, norm):
+    # every length 0..20 appears, in a shuffled order, with repeats
+    rng = np.random.default_rng(11)
+    ms = np.concatenate([np.arange(0, 21), rng.integers(0, 21, 40)]).astype(np.uint8)
+    rng.shuffle(ms)
+    off = W.ragged_offsets(ms)
+    x = np.zeros(off[-1], dtype=np.float32)
+    for i, m in enumerate(ms):
+        x[off[i]: off[i] + (1 << int(m))] = rng.standard_normal(1 << int(m), dtype=np.float32)
+    got, _, p = run(chw, ms, x, "f32", norm, repeats=2)
+    info = chw.chw_plan_get_info(p)
+    assert info.tier == 4 and info.kernels_per_call == 1
+    for i, ref in enumerate(per_signal_ref(ms, off, x, np.float32, norm)):
+        assert_bitwise(got[off[i]: off[i] + ref.size], ref, f"signal {i} m={ms[i]}")
+
+
+def test_ragged_int32_and_in_place(chw):
+    rng = np.random.default_rng(12)
+    ms = rng.integers(0, 21, 30).astype(np.uint8)
+    off = W.ragged_offsets(ms)
+    x = np.zeros(off[-1], dtype=np.int32)
+    for i, m in enumerate(ms):
+        x[off[i]: off[i] + (1 << int(m))] = rng.integers(-(2**9), 2**9, 1 << int(m))
+    got, _, _ = run(chw, ms, x, "i32", "none", inplace=True)
+    for i, m in enumerate(ms):
+        seg = x[off[i]: off[i] + (1 << int(m))].astype(np.int64)
+        ref = O.wht_fast_dyadic(seg, int(m), normalised=False)
+        assert np.array_equal(got[off[i]: off[i] + (1 << int(m))], ref.astype(np.int32)), (i, m)
+
+
+def test_ragged_many_long_signals_reuse_the_ring(chw):
+    # more two-pass signals than ring slots: slots are reused behind dependency waits
+    rng = np.random.default_rng(13)
+    ms = rng.integers(15, 19, 40).astype(np.uint8)
+    off = W.ragged_offsets(ms)
+    x = rng.standard_normal(off[-1], dtype=np.float32)
+    got, _, _ = run(chw, ms, x, "f32", "end", repeats=3)
+    for i in rng.choice(len(ms), 8, replace=False):
+        ref = O.chw_cascade(x[off[i]: off[i] + (1 << int(ms[i]))][None, :], int(ms[i]), np.float32, "end")[0]
+        assert_bitwise(got[off[i]: off[i] + ref.size], ref, f"signal {i} m={ms[i]}")
+
+
+def test_ragged_config_10000_signals(chw):
+    ms, off, x = W.ragged_normal_f32(10000, 5)
+    got, _, p = run(chw, ms, x, "f32", "end")
+    rng = np.random.default_rng(0)
+    pick = list(rng.choice(len(ms), 12, replace=False)) + [int(np.argmax(ms)), int(np.argmin(ms))]
+    for i in pick:
+        seg = x[off[i]: off[i] + (1 << int(ms[i]))]
+        ref = O.chw_cascade(seg[None, :], int(ms[i]), np.float32, "end")[0]
+        assert_bitwise(got[off[i]: off[i] + ref.size], ref, f"signal {i} m={ms[i]}")
+        err = O.rel_err_per_signal(got[off[i]: off[i] + ref.size], O.wht_fast_dyadic(seg.astype(np.float64), int(ms[i])))
+        assert err.max() <= 1e-6
