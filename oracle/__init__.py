@@ -48,7 +48,7 @@ from .transforms import (
     end_scale_f32,
     inv_sqrt2,
 )
-from .lowp import lowp_forward_reference, round_to_bf16, round_to_f16, dequantise
+from .lowp import codes_to_f32, dequantise, lowp_forward_reference, round_to_bf16, round_to_f16
 from .errors import rel_err_per_signal
 
 __all__ = [
@@ -73,5 +73,6 @@ __all__ = [
     "round_to_bf16",
     "round_to_f16",
     "dequantise",
+    "codes_to_f32",
     "rel_err_per_signal",
 ]

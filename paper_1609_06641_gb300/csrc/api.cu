@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -42,15 +43,27 @@ struct Shape {
   int tb, cb;
 };
 
+// Tile bits preferred for cluster shapes: 14 (64 KiB tiles, one CTA per SM) or 13
+// (32 KiB tiles in twice as many CTAs, three per SM); CHW_CLUSTER_TILE_BITS overrides.
+int cluster_tile_bits() {
+  static const int v = [] {
+    const char* e = std::getenv("CHW_CLUSTER_TILE_BITS");
+    return (e && std::atoi(e) == 13) ? 13 : 14;
+  }();
+  return v;
+}
+
 // One-pass row kernel shape for a transform of M bits.
 Shape row_shape(int M) {
   if (M <= 13) return {13, 0};
+  if (M <= 16 && cluster_tile_bits() == 13) return {13, M - 13};
   if (M == 14) return {14, 0};
   return {14, M - 14};
 }
 // Second-pass column kernel shape for A row bits (32 columns per block).
 Shape col_shape(int A) {
   if (A <= 8) return {13, 0};
+  if (A <= 11 && cluster_tile_bits() == 13) return {13, A - 8};
   if (A == 9) return {14, 0};
   return {14, A - 9};
 }
@@ -97,6 +110,16 @@ chw_status_t make_rows_map(CUtensorMap* map, const void* ptr, int64_t total, int
 }
 
 }  // namespace
+
+namespace chw {
+int64_t persistent_cap_override() {
+  static const int64_t v = [] {
+    const char* e = std::getenv("CHW_MAX_RESIDENT_UNITS");
+    return e ? std::atoll(e) : int64_t{0};
+  }();
+  return v;
+}
+}  // namespace chw
 
 struct chw_plan_s {
   int device = 0;
@@ -158,9 +181,9 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
   a.diag_mask = diag_mask;
   a.status = p->d_status;
   a.colblock_a = colblock_a;
-  const int64_t tile = int64_t{1} << s.tb;
-  const int64_t ctas = s.cb > 0 ? total / tile : (total + tile - 1) / tile;
-  CHW_CUDA(fn(&map, a, ctas, st));
+  const int64_t unit = int64_t{1} << (s.tb + s.cb);
+  const int64_t units = s.cb > 0 ? total / unit : (total + unit - 1) / unit;
+  CHW_CUDA(fn(&map, a, units, st));
   return CHW_OK;
 }
 
@@ -181,9 +204,9 @@ chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, const void* in, void
   a.diag_mask = diag_mask;
   a.status = p->d_status;
   a.colblock_a = 0;
-  const int64_t tile = int64_t{1} << s.tb;
-  const int64_t ctas = s.cb > 0 ? total / tile : (total + tile - 1) / tile;
-  CHW_CUDA(fn(&map, a, ctas, st));
+  const int64_t unit = int64_t{1} << (s.tb + s.cb);
+  const int64_t units = s.cb > 0 ? total / unit : (total + unit - 1) / unit;
+  CHW_CUDA(fn(&map, a, units, st));
   return CHW_OK;
 }
 

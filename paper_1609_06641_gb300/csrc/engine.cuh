@@ -267,7 +267,9 @@ __device__ __forceinline__ void load_phase_cluster(uint32_t (&v)[64], const uint
   });
 }
 
-// Butterflies of phase P on the label bits in [LO, HI), lowest bit first.
+// Butterflies of phase P on the label bits in [LO, HI), lowest bit first.  When the
+// functor has a packed form (two butterflies in one f32x2 instruction pair) and register
+// bit 0 is not the butterfly bit, registers k and k|1 travel together.
 template <Phase P, int LO, int HI, class BF>
 __device__ __forceinline__ void butterflies(uint32_t (&v)[64], const BF& bf) {
   sfor<kMaxBits>([&](auto bb) {
@@ -275,38 +277,69 @@ __device__ __forceinline__ void butterflies(uint32_t (&v)[64], const BF& bf) {
     if constexpr (b >= LO && b < HI) {
       constexpr int i = reg_index_of(P, b);
       static_assert(i >= 0, "a butterfly bit must be a register bit of its phase");
-      sfor<64>([&](auto kk) {
-        constexpr int k = kk;
-        if constexpr (((k >> i) & 1) == 0) bf(v[k], v[k | (1 << i)]);
-      });
+      if constexpr (BF::kPacked && i >= 1) {
+        sfor<64>([&](auto kk) {
+          constexpr int k = kk;
+          if constexpr (((k >> i) & 1) == 0 && (k & 1) == 0)
+            bf.pair(v[k], v[k | 1], v[k | (1 << i)], v[k | 1 | (1 << i)]);
+        });
+      } else {
+        sfor<64>([&](auto kk) {
+          constexpr int k = kk;
+          if constexpr (((k >> i) & 1) == 0) bf(v[k], v[k | (1 << i)]);
+        });
+      }
     }
   });
 }
 
-// Butterfly (a, b) -> (a+b, a-b), values carried as 32-bit patterns.
+// Butterfly (a, b) -> (a+b, a-b), values carried as 32-bit patterns.  The packed form
+// runs two butterflies with f32x2 instructions (per-lane IEEE round to nearest even, no
+// flush of subnormals: the same results as the scalar form).
 struct BfF32Plain {
+  static constexpr bool kPacked = true;
   __device__ __forceinline__ void operator()(uint32_t& a, uint32_t& b) const {
     const float x = __uint_as_float(a), y = __uint_as_float(b);
     a = __float_as_uint(__fadd_rn(x, y));
     b = __float_as_uint(__fsub_rn(x, y));
   }
+  __device__ __forceinline__ void pair(uint32_t& a0, uint32_t& a1, uint32_t& b0, uint32_t& b1) const {
+    asm("{\n\t.reg .b64 x, y, s, d;\n\t"
+        "mov.b64 x, {%4, %5};\n\tmov.b64 y, {%6, %7};\n\t"
+        "add.rn.f32x2 s, x, y;\n\tsub.rn.f32x2 d, x, y;\n\t"
+        "mov.b64 {%0, %1}, s;\n\tmov.b64 {%2, %3}, d;\n\t}"
+        : "=r"(a0), "=r"(a1), "=r"(b0), "=r"(b1)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+  }
 };
 // (a, b) -> ((a+b) c, (a-b) c), each operation rounded to nearest even.
 struct BfF32PerLevel {
+  static constexpr bool kPacked = true;
   float c;
   __device__ __forceinline__ void operator()(uint32_t& a, uint32_t& b) const {
     const float x = __uint_as_float(a), y = __uint_as_float(b);
     a = __float_as_uint(__fmul_rn(__fadd_rn(x, y), c));
     b = __float_as_uint(__fmul_rn(__fsub_rn(x, y), c));
   }
+  __device__ __forceinline__ void pair(uint32_t& a0, uint32_t& a1, uint32_t& b0, uint32_t& b1) const {
+    asm("{\n\t.reg .b64 x, y, s, d, cc;\n\t"
+        "mov.b64 x, {%4, %5};\n\tmov.b64 y, {%6, %7};\n\tmov.b64 cc, {%8, %8};\n\t"
+        "add.rn.f32x2 s, x, y;\n\tsub.rn.f32x2 d, x, y;\n\t"
+        "mul.rn.f32x2 s, s, cc;\n\tmul.rn.f32x2 d, d, cc;\n\t"
+        "mov.b64 {%0, %1}, s;\n\tmov.b64 {%2, %3}, d;\n\t}"
+        : "=r"(a0), "=r"(a1), "=r"(b0), "=r"(b1)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1), "r"(__float_as_uint(c)));
+  }
 };
 // int32 with two's-complement wrap (unsigned arithmetic).
 struct BfI32 {
+  static constexpr bool kPacked = false;
   __device__ __forceinline__ void operator()(uint32_t& a, uint32_t& b) const {
     const uint32_t x = a, y = b;
     a = x + y;
     b = x - y;
   }
+  __device__ __forceinline__ void pair(uint32_t&, uint32_t&, uint32_t&, uint32_t&) const {}
 };
 
 }  // namespace chw

@@ -249,20 +249,33 @@ struct FusedCfg {
 };
 
 // ------------------------------------------------------------------ one tile
-// Transform the (cluster) tile whose input starts at TMA row `in_row0` (rows of 32 words)
-// and whose outputs start at element `out_base`.  `buf` is this CTA's 1024-byte aligned
-// 2^TB-word shared buffer, `bar` an initialised mbarrier whose next phase has `parity`.
-// All threads of the CTA call this; it ends with the CTA's output stores issued.
+// Issue the TMA load of a (CTA's part of a) tile: rows [in_row0, in_row0 + 2^(TB-5)) of
+// 32 words into `buf`, completing on `bar`.  One thread calls this.  Earlier
+// generic-proxy accesses to `buf` must be ordered before it by a barrier.
+template <int TB>
+__device__ __forceinline__ void tile_issue(const CUtensorMap* tin, int in_row0, uint32_t* buf, uint64_t* bar) {
+  constexpr int BOXR = (1 << (TB - 5)) < 256 ? (1 << (TB - 5)) : 256;
+  constexpr int NBOX = (1 << (TB - 5)) / BOXR;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const uint64_t pol = policy_evict_first();
+  mbar_arrive_expect_tx(bar, 4u << TB);
+#pragma unroll
+  for (int j = 0; j < NBOX; ++j) tma_load_2d(buf + j * BOXR * 32, tin, bar, 0, in_row0 + j * BOXR, pol);
+}
+
+// Transform the (cluster) tile held in `buf` once `bar` completes phase `parity`: the
+// input's first element is `in_elem0` (for the adjoint's diagonal) and the outputs start
+// at element `out_base`.  All threads of the CTA call this; it returns with the CTA's
+// output stores issued and `buf` no longer read by this CTA's threads (a barrier is still
+// needed before `buf` is refilled).
 template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
-__device__ __forceinline__ void fused_tile(const CUtensorMap* tin, int in_row0, int64_t out_base,
-                                           const FusedArgs& args, uint32_t* buf, uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base, const FusedArgs& args,
+                                             uint32_t* buf, uint64_t* bar, uint32_t parity) {
   using Cfg = FusedCfg<TLO, M, TB, CB>;
   constexpr FusedPlan F = Cfg::plan;
   constexpr int NT = 1 << (TB - 6);
   constexpr int NR = 1 << CB;
   constexpr uint32_t LMASK = Cfg::LMASK;
-  constexpr int BOXR = (1 << (TB - 5)) < 256 ? (1 << (TB - 5)) : 256;
-  constexpr int NBOX = (1 << (TB - 5)) / BOXR;
   constexpr Phase P1 = F.p1, P2 = F.p2, P3 = F.p3, FW = F.fw;
   constexpr Lin LS = F.lin_s, LB = F.lin_b, LF = F.lin_final;
 
@@ -272,14 +285,6 @@ __device__ __forceinline__ void fused_tile(const CUtensorMap* tin, int in_row0, 
   BF bf{};
   if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
 
-  if (tid == 0) {
-    // order earlier generic-proxy accesses to buf before the TMA (async-proxy) writes
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const uint64_t pol = policy_evict_first();
-    mbar_arrive_expect_tx(bar, 4u << TB);
-#pragma unroll
-    for (int j = 0; j < NBOX; ++j) tma_load_2d(buf + j * BOXR * 32, tin, bar, 0, in_row0 + j * BOXR, pol);
-  }
   if (!mbar_wait_bounded(bar, parity, kWaitTries)) {
     if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
   }
@@ -297,10 +302,9 @@ __device__ __forceinline__ void fused_tile(const CUtensorMap* tin, int in_row0, 
     load_phase<P1, LS, LMASK>(v, buf, base);
     if (args.diag_in != nullptr) {
       const uint32_t tl = thread_label<P1>(lane, warp, 0);
-      const int64_t in0 = static_cast<int64_t>(in_row0) * 32;
       sfor<64>([&](auto k) {
         constexpr uint32_t kl = reg_label(P1, k);
-        const int64_t idx = in0 + (tl | kl);
+        const int64_t idx = in_elem0 + (tl | kl);
         if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
       });
     }
@@ -404,28 +408,62 @@ __device__ __forceinline__ void fused_tile(const CUtensorMap* tin, int in_row0, 
   }
 }
 
+// Load + transform one tile (the persistent ragged kernel's form: no prefetch).
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
+__device__ __forceinline__ void fused_tile(const CUtensorMap* tin, int in_row0, int64_t out_base,
+                                           const FusedArgs& args, uint32_t* buf, uint64_t* bar, uint32_t parity) {
+  if (threadIdx.x == 0) tile_issue<TB>(tin, in_row0, buf, bar);
+  tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(static_cast<int64_t>(in_row0) * 32, out_base, args, buf, bar,
+                                                     parity);
+}
+
 // 1024-byte aligned start of the dynamic shared buffer (SWIZZLE_128B needs it).
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   const uint32_t a = smem_u32(p);
   return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
+// CTAs per SM the batched kernel is compiled for: two 2^TB-word buffers per CTA.
+template <int TB>
+constexpr int fused_ctas_per_sm() {
+  return TB >= 14 ? 1 : 3;
+}
+
 // ------------------------------------------------------------------ the batched kernel
+// Persistent: each CTA (cluster) walks the units u = first, first + stride, ... with two
+// shared buffers; the TMA load of unit k+1 is issued before unit k is transformed, so HBM
+// reads overlap the butterflies and the stores of the previous unit.
 template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
-__global__ void __launch_bounds__(1 << (TB - 6), (TB >= 14 ? 2 : 4))
-    fused_kernel(const __grid_constant__ CUtensorMap tin, const FusedArgs args) {
+__global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
+    fused_kernel(const __grid_constant__ CUtensorMap tin, const FusedArgs args, const int64_t units) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
-  uint32_t* buf = reinterpret_cast<uint32_t*>(base);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (4u << TB));
+  uint32_t* buf0 = reinterpret_cast<uint32_t*>(base);
+  uint32_t* buf1 = buf0 + (1u << TB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (8u << TB));
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  const int64_t tile = blockIdx.x;
-  const int64_t out_base = CB > 0 ? ((tile >> CB) << (TB + CB)) : (tile << TB);
-  fused_tile<TLO, M, TB, CB, BF, SCALE, OUTMODE>(&tin, static_cast<int>(tile << (TB - 5)), out_base, args, buf, bar, 0u);
+  const uint32_t rank = CB > 0 ? cluster_ctarank() : 0u;
+  const int64_t stride = gridDim.x >> CB;
+  const int64_t first = blockIdx.x >> CB;
+  // input rows of unit u for this CTA (a cluster's CTAs split a unit into 2^CB slices)
+  auto row0 = [&](int64_t u) { return static_cast<int>(((u << CB) | rank) << (TB - 5)); };
+  if (threadIdx.x == 0 && first < units) tile_issue<TB>(&tin, row0(first), buf0, bar);
+  int k = 0;
+  for (int64_t u = first; u < units; u += stride, ++k) {
+    uint32_t* cur = (k & 1) ? buf1 : buf0;
+    uint32_t* nxt = (k & 1) ? buf0 : buf1;
+    const int64_t un = u + stride;
+    if (threadIdx.x == 0 && un < units) tile_issue<TB>(&tin, row0(un), nxt, bar + ((k + 1) & 1));
+    const int64_t out_base = CB > 0 ? (u << (TB + CB)) : (u << TB);
+    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(static_cast<int64_t>(row0(u)) * 32, out_base, args, cur,
+                                                     bar + (k & 1), (k >> 1) & 1);
+    __syncthreads();
+  }
 }
 
 }  // namespace chw

@@ -15,22 +15,58 @@ enum FusedVariant {
   kVarI32 = 3        // int32, unscaled, wrapping
 };
 
-using FusedLaunchFn = cudaError_t (*)(const CUtensorMap* tin, const FusedArgs& args, int64_t ctas, cudaStream_t st);
+// `units`: number of (cluster) tiles; the launcher sizes a persistent grid.
+using FusedLaunchFn = cudaError_t (*)(const CUtensorMap* tin, const FusedArgs& args, int64_t units, cudaStream_t st);
 
 template <int TB>
 constexpr int fused_smem_bytes() {
-  return (4 << TB) + 1024 + 64;
+  return (8 << TB) + 1024 + 64;  // two tile buffers, alignment slack, two mbarriers
 }
 
+// Units the device keeps resident at once for this kernel (0 if the query fails).
+template <class K>
+int64_t resident_units(K kern, int threads, int smem, int cluster) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cluster <= 1) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return 0;
+    return static_cast<int64_t>(per_sm) * sms;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(static_cast<unsigned>(cluster), 1, 1);
+  cfg.blockDim = dim3(static_cast<unsigned>(threads), 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = static_cast<unsigned>(cluster);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) return 0;
+  return nc;
+}
+
+int64_t persistent_cap_override();  // CHW_MAX_RESIDENT_UNITS, 0 = none (tuning)
+
 template <int TLO, int M, int TB, int CB, class BF, bool SC, int OM>
-cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t ctas, cudaStream_t st) {
+cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t units, cudaStream_t st) {
   auto kern = fused_kernel<TLO, M, TB, CB, BF, SC, OM>;
   constexpr int smem = fused_smem_bytes<TB>();
+  constexpr int threads = 1 << (TB - 6);
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (attr != cudaSuccess) return attr;
+  static const int64_t resident = resident_units(kern, threads, smem, 1 << CB);
+  int64_t grid_units = units;
+  int64_t cap = persistent_cap_override();
+  if (cap <= 0) cap = resident;
+  if (cap > 0 && grid_units > cap) grid_units = cap;
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(static_cast<unsigned>(ctas), 1, 1);
-  cfg.blockDim = dim3(1u << (TB - 6), 1, 1);
+  cfg.gridDim = dim3(static_cast<unsigned>(grid_units << CB), 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
@@ -42,7 +78,7 @@ cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t 
     cfg.attrs = at;
     cfg.numAttrs = 1;
   }
-  return cudaLaunchKernelEx(&cfg, kern, *tin, args);
+  return cudaLaunchKernelEx(&cfg, kern, *tin, args, units);
 }
 
 // Kernel for one fused shape and variant (nullptr if that shape was not compiled).  The

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kRaggedThreads, 2)
 template <int VAR>
 cudaError_t launch_ragged(const CUtensorMap& tx, const CUtensorMap& tr, const RaggedArgs& a, cudaStream_t st) {
   auto kern = ragged_kernel<VAR>;
-  constexpr int smem = fused_smem_bytes<kRaggedTileBits>();
+  constexpr int smem = (4 << kRaggedTileBits) + 1024 + 64;  // one tile buffer + mbarrier
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (attr != cudaSuccess) return attr;
   int dev = 0, sms = 0, per_sm = 0;
