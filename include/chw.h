@@ -78,7 +78,7 @@ typedef struct chw_plan_info_s {
   int64_t batch;             /* signals per call (ragged: number of signals)          */
   int dtype;                 /* chw_dtype_t                                            */
   int norm;                  /* chw_norm_t                                             */
-  int tier;                  /* 0 simple, 1 fused CTA, 2 fused cluster, 3 two-pass, 4 ragged */
+  int tier;                  /* 0 simple, 1 fused CTA, 2 fused cluster, 3 two-pass, 4 ragged, 5 fused 16-bit */
   int passes;                /* HBM round trips per call                               */
   int row_bits;              /* two-pass: bits transformed in pass 1 (else m)          */
   int cluster;               /* CTAs per cluster in the fused (or first) pass          */
@@ -106,8 +106,10 @@ chw_status_t chw_plan(chw_plan_t* plan, int m, int64_t batch, chw_dtype_t dtype,
  * chw_plan_ragged -- prepare one call over `count` signals of uneven lengths 2^{ms[i]}
  * (the transform of eq. (1) applied to each signal independently).
  *   ms_host   host array of `count` bit counts, each in 0..20.  The signals are packed
- *             back to back in that order: signal i starts at element offset
- *             sum_{j<i} 2^{ms[j]} (chw_ragged_offsets() returns these offsets).
+ *             in that order, each starting on a 32-element (128-byte) boundary:
+ *             offset[0] = 0, offset[i+1] = round_up(offset[i] + 2^{ms[i]}, 32); signals
+ *             with m >= 5 therefore pack back to back (chw_ragged_offsets() returns the
+ *             offsets; the padding elements are neither read into results nor written).
  *   dtype     CHW_F32 or CHW_I32 (with norm as for chw_plan).
  * The plan builds its task table and device work queue once; chw_forward_ragged() then
  * runs every signal in one persistent launch, replayed from a CUDA graph.

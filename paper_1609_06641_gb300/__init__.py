@@ -32,7 +32,7 @@ from ._lib import (
 
 DTYPES = {"i32": CHW_I32, "f32": CHW_F32, "bf16": CHW_BF16, "f16": CHW_F16}
 NORMS = {"none": CHW_NORM_NONE, "per_level": CHW_NORM_PER_LEVEL, "end": CHW_NORM_END}
-TIERS = {0: "simple", 1: "fused", 2: "cluster", 3: "two-pass", 4: "ragged"}
+TIERS = {0: "simple", 1: "fused", 2: "cluster", 3: "two-pass", 4: "ragged", 5: "fused-16bit"}
 
 
 def _torch_dtype(code):

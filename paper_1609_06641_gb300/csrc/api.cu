@@ -16,6 +16,12 @@
 #include "launch.cuh"
 #include "ragged.cuh"
 #include "simple.cuh"
+#include "lowp.cuh"
+
+namespace chw {
+using LowpLaunchFn = cudaError_t (*)(const CUtensorMap*, const LowpArgs&, int64_t, cudaStream_t);
+LowpLaunchFn lookup_lowp(int m, bool f16, bool end);
+}  // namespace chw
 
 namespace {
 
@@ -37,7 +43,7 @@ chw_status_t fail(chw_status_t s, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(CHW_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
   } while (0)
 
-enum Tier { kTierSimple = 0, kTierFused = 1, kTierCluster = 2, kTierTwoPass = 3, kTierRagged = 4 };
+enum Tier { kTierSimple = 0, kTierFused = 1, kTierCluster = 2, kTierTwoPass = 3, kTierRagged = 4, kTierLowp = 5 };
 
 struct Shape {
   int tb, cb;
@@ -210,6 +216,40 @@ chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, const void* in, void
   return CHW_OK;
 }
 
+// `batch` signals of 2^m 2-byte codes viewed as rows of 64 codes (128 B), SWIZZLE_128B.
+chw_status_t make_codes_map(CUtensorMap* map, const void* ptr, int64_t batch, int m) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[2] = {64, static_cast<cuuint64_t>((batch << m) / 64)};
+  cuuint64_t strides[1] = {128};
+  cuuint32_t box[2] = {64, static_cast<cuuint32_t>(1 << (m - 6))};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return CHW_OK;
+}
+
+chw_status_t launch_lowp_fused(chw_plan_s* p, const void* x, void* y, int64_t batch, const int32_t* exp_in,
+                               int32_t* exp_out, const int8_t* diag_in, const int8_t* diag_out, cudaStream_t st) {
+  chw::LowpLaunchFn fn = chw::lookup_lowp(p->m, p->dtype == CHW_F16, p->norm == CHW_NORM_END);
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no fused 16-bit kernel for m=%d", p->m);
+  CUtensorMap map;
+  chw_status_t r = make_codes_map(&map, x, batch, p->m);
+  if (r != CHW_OK) return r;
+  chw::LowpArgs a{};
+  a.out = y;
+  a.exp_in = exp_in;
+  a.exp_out = exp_out;
+  a.end_scale = end_scale_f32(p->m);
+  a.diag_in = diag_in;
+  a.diag_out = diag_out;
+  a.status = p->d_status;
+  CHW_CUDA(fn(&map, a, batch, st));
+  return CHW_OK;
+}
+
 chw_status_t launch_simple(chw_plan_s* p, const void* x, void* y, int64_t batch, const int32_t* exp_in,
                            int32_t* exp_out, const int8_t* diag_in, const int8_t* diag_out, cudaStream_t st) {
   chw::SimpleArgs a{};
@@ -248,6 +288,8 @@ chw_status_t run_transform(chw_plan_s* p, const void* x, void* y, int64_t batch,
   switch (p->tier) {
     case kTierSimple:
       return launch_simple(p, x, y, batch, exp_in, exp_out, diag_in, diag_out, st);
+    case kTierLowp:
+      return launch_lowp_fused(p, x, y, batch, exp_in, exp_out, diag_in, diag_out, st);
     case kTierFused:
     case kTierCluster:
       return launch_row_pass(p, m, 0, fused_variant(p, true), x, y, total, diag_in, diag_out, dmask, 0,
@@ -334,7 +376,7 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
       delete p;
       return fail(CHW_ERR_UNSUPPORTED, "bf16/fp16 storage needs m <= 13 (one CTA per signal)");
     }
-    p->tier = kTierSimple;
+    p->tier = (m == 11 || m == 12) && (flags & CHW_FLAG_FORCE_SIMPLE) == 0 ? kTierLowp : kTierSimple;
   } else if ((flags & CHW_FLAG_FORCE_SIMPLE) != 0) {
     if (m > 13) {
       delete p;

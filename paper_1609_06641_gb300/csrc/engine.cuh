@@ -253,6 +253,21 @@ __device__ __forceinline__ void store_phase(const uint32_t (&v)[64], uint32_t* b
   }
 }
 
+// Store the values (indexed in phase PR's order) with 16-byte stores into the shared memory
+// of the cluster CTA whose buffer starts at cluster address `rbase`, at positions MAP(label).
+template <Phase PW, Phase PR, Lin MAP>
+__device__ __forceinline__ void store_phase_remote(const uint32_t (&v)[64], uint32_t rbase, uint32_t base) {
+  static_assert(v4_ok(PW, MAP, ~0u), "remote stores move 16-byte chunks");
+  sfor<16>([&](auto j) {
+    constexpr int k = 4 * j;
+    constexpr uint32_t kp = apply(MAP, reg_label(PW, k));
+    constexpr int r0 = remap_index(PR, PW, k), r1 = remap_index(PR, PW, k + 1);
+    constexpr int r2 = remap_index(PR, PW, k + 2), r3 = remap_index(PR, PW, k + 3);
+    static_assert(r0 >= 0 && r1 >= 0 && r2 >= 0 && r3 >= 0, "write order must hold the same labels");
+    st_dsmem_v4(rbase + 4u * (base ^ kp), v[r0], v[r1], v[r2], v[r3]);
+  });
+}
+
 // Load phase P's values from the cluster: label bits >= TB pick the CTA rank whose shared
 // memory (at the same layout MAP) holds them; rbase[r] is that CTA's buffer address.
 template <Phase P, Lin MAP, int TB, int NR>
@@ -312,7 +327,10 @@ struct BfF32Plain {
         : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
   }
 };
-// (a, b) -> ((a+b) c, (a-b) c), each operation rounded to nearest even.
+// (a, b) -> ((a+b) c, (a-b) c), each operation rounded to nearest even.  The packed form
+// adds and subtracts with f32x2 but multiplies with scalar mul.rn: a packed multiply feeding
+// the next level's packed add was observed to be fused into one FMA by the assembler (a
+// GB300 probe of chained levels), which would round differently from the cascade.
 struct BfF32PerLevel {
   static constexpr bool kPacked = true;
   float c;
@@ -322,13 +340,11 @@ struct BfF32PerLevel {
     b = __float_as_uint(__fmul_rn(__fsub_rn(x, y), c));
   }
   __device__ __forceinline__ void pair(uint32_t& a0, uint32_t& a1, uint32_t& b0, uint32_t& b1) const {
-    asm("{\n\t.reg .b64 x, y, s, d, cc;\n\t"
-        "mov.b64 x, {%4, %5};\n\tmov.b64 y, {%6, %7};\n\tmov.b64 cc, {%8, %8};\n\t"
-        "add.rn.f32x2 s, x, y;\n\tsub.rn.f32x2 d, x, y;\n\t"
-        "mul.rn.f32x2 s, s, cc;\n\tmul.rn.f32x2 d, d, cc;\n\t"
-        "mov.b64 {%0, %1}, s;\n\tmov.b64 {%2, %3}, d;\n\t}"
-        : "=r"(a0), "=r"(a1), "=r"(b0), "=r"(b1)
-        : "r"(a0), "r"(a1), "r"(b0), "r"(b1), "r"(__float_as_uint(c)));
+    BfF32Plain{}.pair(a0, a1, b0, b1);
+    a0 = __float_as_uint(__fmul_rn(__uint_as_float(a0), c));
+    a1 = __float_as_uint(__fmul_rn(__uint_as_float(a1), c));
+    b0 = __float_as_uint(__fmul_rn(__uint_as_float(b0), c));
+    b1 = __float_as_uint(__fmul_rn(__uint_as_float(b1), c));
   }
 };
 // int32 with two's-complement wrap (unsigned arithmetic).

@@ -39,7 +39,8 @@ struct FusedArgs {
 struct FusedPlan {
   bool has_p1, has_p3, p1_final, p2_final;
   Phase p1, p2, p3, fw;  // fw: the final phase in output-write register order
-  Lin lin_s, lin_b, lin_final;
+  Phase p2w;             // phase 2 in push order (clusters)
+  Lin lin_s, lin_b, lin_final, lin_r;
   bool b_is_s;
   int stage_s;
   Lin omap;
@@ -90,12 +91,13 @@ constexpr Phase make_p3(int TB, int CB, int TLO, int M) {
   Phase p{};
   const int nb = TB + CB;
   const int top = TLO + M - 1;
-  // CTA-rank and lane bits per (TLO, CB); see the bank analysis in the file comment of
-  // engine.cuh.  Lane bits 0..2 (a quarter warp) feed the staging swizzle key.
+  // CTA-rank and lane bits per (TLO, CB).  Lane bits 0..2 (a quarter warp) set the staging
+  // swizzle key; in a cluster two of the lanes are phase-2 register labels so that phase 2
+  // can push 16-byte chunks to the CTA that finishes them.
   const int ctas[2][4][3] = {{{-1, -1, -1}, {0, -1, -1}, {0, 1, -1}, {0, 1, 2}},
                              {{-1, -1, -1}, {4, -1, -1}, {4, 3, -1}, {4, 3, 2}}};
-  const int lanes[2][4][5] = {{{4, 3, 2, 1, 0}, {4, 3, 2, 1, 5}, {4, 3, 2, 5, 6}, {5, 4, 3, 6, 7}},
-                              {{4, 3, 2, 1, 0}, {0, 1, 2, 3, 5}, {0, 1, 2, 5, 6}, {0, 1, 5, 6, 7}}};
+  const int lanes[2][4][5] = {{{4, 3, 2, 1, 0}, {4, 3, 2, 5, 6}, {4, 3, 2, 5, 6}, {5, 4, 3, 6, 7}},
+                              {{4, 3, 2, 1, 0}, {1, 2, 3, 5, 6}, {0, 1, 2, 5, 6}, {0, 1, 5, 6, 7}}};
   const int t = TLO == 0 ? 0 : 1;
   bool used[kMaxBits] = {};
   p.ncta = CB;
@@ -167,6 +169,76 @@ constexpr Lin make_lin_b(const Phase& p2, const Phase& p3) {
   return l;
 }
 
+// Receive layout of the cluster exchange (phase 2 -> phase 3), on the labels a CTA
+// finishes (its CTA-rank labels map to nothing): word bits 0,1 hold two phase-3 lane labels
+// that are phase-2 registers (16-byte pushes), bits 2..4 the other phase-3 lanes (conflict-
+// free phase-3 reads), then the remaining labels in increasing order.
+constexpr Lin make_lin_r(const Phase& p2, const Phase& p3, int nb) {
+  Lin l{};
+  int order[kMaxBits] = {};
+  int n = 0, na = 0;
+  int ab[2] = {-1, -1};
+  for (int j = 0; j < 5 && na < 2; ++j)
+    if (reg_index_of(p2, p3.lane[j]) >= 0) ab[na++] = p3.lane[j];
+  if (na < 2) return lin_identity();  // rejected by the static checks of FusedCfg
+  order[n++] = ab[0];
+  order[n++] = ab[1];
+  for (int j = 0; j < 5; ++j)
+    if (p3.lane[j] != ab[0] && p3.lane[j] != ab[1]) order[n++] = p3.lane[j];
+  for (int b = 0; b < nb; ++b) {
+    bool skip = false;
+    for (int i = 0; i < n; ++i) skip |= order[i] == b;
+    for (int i = 0; i < p3.ncta; ++i) skip |= p3.cta[i] == b;
+    if (!skip) order[n++] = b;
+  }
+  for (int i = 0; i < n; ++i) l.img[order[i]] = 1u << i;
+  return l;
+}
+
+// Phase 2's write order for the pushes: registers 0 and 1 hold the labels at word bits 0, 1.
+constexpr Phase push_order(const Phase& p2, const Lin& r) {
+  int l0 = -1, l1 = -1;
+  for (int i = 0; i < p2.nreg; ++i) {
+    if (r.img[p2.reg[i]] == 1u) l0 = p2.reg[i];
+    if (r.img[p2.reg[i]] == 2u) l1 = p2.reg[i];
+  }
+  Phase q = p2;
+  if (l0 < 0 || l1 < 0) return q;
+  q.reg[0] = l0;
+  q.reg[1] = l1;
+  int n = 2;
+  for (int i = 0; i < p2.nreg; ++i)
+    if (p2.reg[i] != l0 && p2.reg[i] != l1) q.reg[n++] = p2.reg[i];
+  return q;
+}
+
+// Worst conflict degree of the 16-byte pushes: lanes of a quarter warp that go to the same
+// CTA must hit distinct 16-byte bank groups.  `src` is the label bits of the pushing CTA.
+constexpr int push_conflicts(const Phase& pw, const Lin& r, const Phase& p3) {
+  int worst = 1;
+  for (int k = 0; k < 64; k += 4)
+    for (int q = 0; q < 4; ++q)
+      for (int d = 0; d < 8; ++d) {
+        int count[8] = {};
+        for (int ln = 8 * q; ln < 8 * q + 8; ++ln) {
+          const uint32_t lab = reg_label(pw, k) | lane_label(pw, ln);
+          int dest = 0;
+          for (int i = 0; i < p3.ncta; ++i) dest |= static_cast<int>((lab >> p3.cta[i]) & 1u) << i;
+          if (dest != d) continue;
+          count[(apply(r, lab) >> 2) & 7]++;
+        }
+        for (int b = 0; b < 8; ++b) worst = count[b] > worst ? count[b] : worst;
+      }
+  return worst;
+}
+
+// The CTA-rank labels of phase 3 are lane or warp labels of phase 2 (one destination per thread).
+constexpr bool push_dest_per_thread(const Phase& p2, const Phase& p3) {
+  for (int i = 0; i < p3.ncta; ++i)
+    if (reg_index_of(p2, p3.cta[i]) >= 0) return false;
+  return true;
+}
+
 constexpr bool lin_equal(const Lin& a, const Lin& b) {
   for (int i = 0; i < kMaxBits; ++i)
     if (a.img[i] != b.img[i]) return false;
@@ -201,6 +273,8 @@ constexpr FusedPlan make_plan(int TLO, int M, int TB, int CB) {
   f.omap = make_omap(TLO, M);
   f.lin_s = lin_tma128();
   f.lin_b = make_lin_b(f.p2, f.p3);
+  f.lin_r = CB > 0 ? make_lin_r(f.p2, f.p3, TB + CB) : lin_identity();
+  f.p2w = push_order(f.p2, f.lin_r);
   f.b_is_s = lin_equal(f.lin_b, f.lin_s);
   const Phase fin = f.p1_final ? f.p1 : (f.p2_final ? f.p2 : f.p3);
   f.fw = write_order(fin, f.omap);
@@ -236,10 +310,15 @@ struct FusedCfg {
                                  conflict_degree(plan.p1, plan.lin_s, LMASK, true) == 1),
                 "phase 1 reads the TMA tile with conflict-free 16-byte loads");
   static_assert(conflict_degree(plan.p2, plan.lin_s, LMASK, false) == 1, "phase 2 reads are conflict-free");
-  static_assert(!plan.has_p3 || conflict_degree(plan.p2, plan.lin_b, LMASK, false) == 1,
+  static_assert(!plan.has_p3 || CB > 0 || conflict_degree(plan.p2, plan.lin_b, LMASK, false) == 1,
                 "phase 2 writes are conflict-free");
-  static_assert(!plan.has_p3 || conflict_degree(plan.p3, plan.lin_b, LMASK, false) == 1,
+  static_assert(!plan.has_p3 || CB > 0 || conflict_degree(plan.p3, plan.lin_b, LMASK, false) == 1,
                 "phase 3 reads are conflict-free");
+  // clusters: 16-byte pushes from phase 2 to the finishing CTA, local phase-3 reads
+  static_assert(CB == 0 || push_dest_per_thread(plan.p2, plan.p3), "one push destination per thread");
+  static_assert(CB == 0 || v4_ok(plan.p2w, plan.lin_r, ~0u), "pushes are 16-byte chunks");
+  static_assert(CB == 0 || push_conflicts(plan.p2w, plan.lin_r, plan.p3) == 1, "pushes are conflict-free");
+  static_assert(CB == 0 || conflict_degree(plan.p3, plan.lin_r, ~0u, false) == 1, "phase 3 reads are conflict-free");
   // The final phase writes every value it holds (labels from other CTAs included) into
   // its own staging buffer, so no label bit is masked there.
   static constexpr bool final_v4 = v4_ok(plan.fw, plan.lin_final, ~0u);
@@ -328,33 +407,40 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
       __syncthreads();
       store_phase<FW, P2, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
       __syncthreads();
+    } else if constexpr (CB > 0) {
+      // Cluster exchange: push each value to the CTA that finishes it (16-byte DSMEM
+      // stores, fire and forget), then phase 3 reads only local shared memory.
+      constexpr Phase P2W = F.p2w;
+      constexpr Lin LR = F.lin_r;
+      cluster_arrive();  // every CTA has read its tile (the pushes overwrite it)
+      cluster_wait();
+      {
+        const uint32_t tl = thread_label<P2>(lane, warp, 0) | (rank << TB);
+        uint32_t dest = 0;
+#pragma unroll
+        for (int i = 0; i < CB; ++i) dest |= ((tl >> P3.cta[i]) & 1u) << i;
+        uint32_t base = 0;
+#pragma unroll
+        for (int b = 0; b < TB + CB; ++b)
+          if ((tl >> b) & 1u) base ^= LR.img[b];
+        store_phase_remote<P2W, P2, LR>(v, mapa_shared(smem_u32(buf), dest), base);
+      }
+      cluster_arrive();  // the pushes are visible cluster-wide
+      cluster_wait();
+      load_phase<P3, LR, ~0u>(v, buf, thread_pos<P3, LR, ~0u>(lane, warp, rank));
+      butterflies<P3, 11, TLO + M>(v, bf);
+      scale_all();
+      __syncthreads();
+      store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, rank));
+      __syncthreads();
     } else {
       if constexpr (!F.b_is_s) __syncthreads();
       store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
-      if constexpr (CB > 0) {
-        cluster_arrive();
-        cluster_wait();
-      } else {
-        __syncthreads();
-      }
-      const uint32_t base3 = thread_pos<P3, LB, LMASK>(lane, warp, rank);
-      if constexpr (CB > 0) {
-        uint32_t rbase[NR];
-        const uint32_t local = smem_u32(buf);
-#pragma unroll
-        for (int r = 0; r < NR; ++r) rbase[r] = mapa_shared(local, r);
-        load_phase_cluster<P3, LB, TB, NR>(v, rbase, base3);
-        cluster_arrive();
-      } else {
-        load_phase<P3, LB, LMASK>(v, buf, base3);
-      }
+      __syncthreads();
+      load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, rank));
       butterflies<P3, 11, TLO + M>(v, bf);
       scale_all();
-      if constexpr (CB > 0) {
-        cluster_wait();
-      } else {
-        __syncthreads();
-      }
+      __syncthreads();
       store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, rank));
       __syncthreads();
     }

@@ -58,9 +58,23 @@ def check(chw, m, batch, fmt, norm, seed):
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
-@pytest.mark.parametrize("m", [3, 6, 9, 12, 13])
+@pytest.mark.parametrize("m", [3, 6, 9, 11, 12, 13])
 def test_lowp_every_tier_size(chw, fmt, m):
     check(chw, m, 24, fmt, "end", seed=40 + m)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+@pytest.mark.parametrize("m", [11, 12])
+def test_lowp_fused_tier_and_adjoint(chw, fmt, m):
+    import paper_1609_06641_gb300 as mod
+
+    p = mod.chw_plan(m, 4, fmt, "end")
+    assert mod.chw_plan_get_info(p).tier == 5
+    x64 = W.heavy_tailed_f64(m, 40, 60 + m)
+    bits, e_in = W.quantise_pow2(x64, fmt)
+    qb, e_out = run_lowp(chw, bits, e_in, m, fmt, adjoint=True)
+    rb, re = O.lowp_forward_reference(bits, e_in, m, fmt)  # H^T = H, same rounding
+    assert np.array_equal(e_out, re) and np.array_equal(qb, rb)
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
@@ -88,8 +102,8 @@ def test_lowp_config_m12_batch16384(chw, fmt):
     assert err_draw.max() <= 2 * GATES[fmt]
 
 
-def test_lowp_zero_signal_and_diag(chw):
-    m = 10
+@pytest.mark.parametrize("m", [10, 11, 12])
+def test_lowp_zero_signal_and_diag(chw, m):
     x64 = W.heavy_tailed_f64(m, 4, 9)
     x64[2] = 0
     bits, e_in = W.quantise_pow2(x64, "f16")
