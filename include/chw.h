@@ -158,6 +158,29 @@ chw_status_t chw_forward_ragged(chw_plan_t plan, const void* x, void* y, void* s
 chw_status_t chw_forward_host(chw_plan_t plan, const void* x_host, void* y_host, const int32_t* exp_in_host,
                               int32_t* exp_out_host, const int8_t* diag_host);
 
+/*
+ * chw_forward_noalloc -- y = H_m x for `batch` signals through the two-HBM-pass kernels,
+ * without allocating anything.  (The paper has no counterpart; this is a library entry
+ * point for callers that cannot allocate device memory when they transform: work being
+ * captured into a CUDA graph, where cudaMalloc is not allowed; processes whose device
+ * memory belongs to another allocator; and latency-critical code that cannot take
+ * cudaMalloc's implicit synchronisation.)
+ *   m, batch, dtype, norm  as for chw_plan, restricted to 18 <= m <= 22, CHW_F32 or
+ *          CHW_I32, and batch * 2^m <= 2^22 elements: the pass-1 intermediate lives in
+ *          a fixed 16 MiB device array of the library, which every GPU that loads the
+ *          library holds until the process exits.  Larger requests return
+ *          CHW_ERR_INVALID_ARG.
+ *   x, y   device buffers as for chw_forward (16-byte aligned); stream as elsewhere.
+ * No plan object, no cudaMalloc/cudaFree.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make that first
+ * call before any stream capture.  All calls share the array, which keeps the previous
+ * call's contents: calls whose work overlaps on the GPU (different streams, or devices
+ * sharing no order) race on it and must be serialised by the caller.  Bounded-wait
+ * timeouts are recorded in the array's header word, which each call clears first.
+ */
+chw_status_t chw_forward_noalloc(int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm, const void* x, void* y,
+                                 void* stream);
+
 /* Fill *info with what the plan launches. */
 chw_status_t chw_plan_get_info(chw_plan_t plan, chw_plan_info_t* info);
 

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "chw_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "chw_forward_ragged": (ctypes.c_int, [_P, _P, _P, _P]),
     "chw_forward_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "chw_forward_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "chw_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(chw_plan_info_t)]),
     "chw_last_device_status": (ctypes.c_int, [_P]),
     "chw_plan_destroy": (ctypes.c_int, [_P]),
