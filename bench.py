@@ -364,6 +364,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="device timing only (profiling runs)")
     ap.add_argument("--m", type=int, default=M, help="transform bits of the timed workload")
     ap.add_argument("--batch", type=int, default=BATCH, help="signals of the timed workload")
+    ap.add_argument("--flags", type=int, default=0, help="chw_plan flags (e.g. 4: row-stack tier for m = 15..17)")
     args = ap.parse_args()
     world, rank, local = dist_env()
 
@@ -399,7 +400,7 @@ def main():
     x_host = W.normal_f32(m, batch, SEED + rank)  # each rank its own signals
     x = torch.from_numpy(x_host).to(dev)
     y = torch.empty_like(x)
-    plan = chw.chw_plan(m, batch, "f32", "end")
+    plan = chw.chw_plan(m, batch, "f32", "end", args.flags)
     info = chw.chw_plan_get_info(plan)
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
@@ -461,7 +462,8 @@ def main():
             "frac": round(achieved / peak, 4),
             "traffic": traffic_from_profile("fused_m16_cluster4_end"),
             "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else "fallback",
-            "kernel": "fused_kernel<TLO=0,M=16,TB=14,CB=2> (4-CTA cluster per signal)",
+            "kernel": {2: "fused_kernel (4-CTA cluster per signal, DSMEM exchange)",
+                       6: "rowstack_kernel<16> (one CTA per signal, rows through L2)"}.get(info.tier, str(info.tier)),
         },
         "e2e": {
             "value": round(gbs(step_bytes, e2e_s) * world, 1),

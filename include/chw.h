@@ -69,6 +69,8 @@ typedef enum chw_norm_e {
 #define CHW_FLAG_NONE 0u
 #define CHW_FLAG_FORCE_SIMPLE 1u    /* use the plain one-CTA-per-signal kernel (tests)  */
 #define CHW_FLAG_FORCE_MULTIPASS 2u /* split m into two HBM passes even if one fits     */
+#define CHW_FLAG_ROWSTACK 4u        /* m = 15..17: one CTA per signal with its rows through */
+                                    /* L2 instead of a thread-block cluster (DSMEM)        */
 
 typedef struct chw_plan_s* chw_plan_t;
 
@@ -78,7 +80,8 @@ typedef struct chw_plan_info_s {
   int64_t batch;             /* signals per call (ragged: number of signals)          */
   int dtype;                 /* chw_dtype_t                                            */
   int norm;                  /* chw_norm_t                                             */
-  int tier;                  /* 0 simple, 1 fused CTA, 2 fused cluster, 3 two-pass, 4 ragged, 5 fused 16-bit */
+  int tier;                  /* 0 simple, 1 fused CTA, 2 fused cluster, 3 two-pass, 4 ragged,
+                                5 fused 16-bit, 6 row-stack (one CTA, L2-resident rows) */
   int passes;                /* HBM round trips per call                               */
   int row_bits;              /* two-pass: bits transformed in pass 1 (else m)          */
   int cluster;               /* CTAs per cluster in the fused (or first) pass          */

@@ -19,6 +19,7 @@ from ._lib import (
     CHW_BF16,
     CHW_F16,
     CHW_F32,
+    CHW_FLAG_ROWSTACK,
     CHW_FLAG_FORCE_MULTIPASS,
     CHW_FLAG_FORCE_SIMPLE,
     CHW_FLAG_NONE,
@@ -32,7 +33,7 @@ from ._lib import (
 
 DTYPES = {"i32": CHW_I32, "f32": CHW_F32, "bf16": CHW_BF16, "f16": CHW_F16}
 NORMS = {"none": CHW_NORM_NONE, "per_level": CHW_NORM_PER_LEVEL, "end": CHW_NORM_END}
-TIERS = {0: "simple", 1: "fused", 2: "cluster", 3: "two-pass", 4: "ragged", 5: "fused-16bit"}
+TIERS = {0: "simple", 1: "fused", 2: "cluster", 3: "two-pass", 4: "ragged", 5: "fused-16bit", 6: "row-stack"}
 
 
 def _torch_dtype(code):

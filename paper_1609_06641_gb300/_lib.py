@@ -30,6 +30,7 @@ CHW_MAX_M = 30
 CHW_FLAG_NONE = 0
 CHW_FLAG_FORCE_SIMPLE = 1
 CHW_FLAG_FORCE_MULTIPASS = 2
+CHW_FLAG_ROWSTACK = 4
 
 
 class chw_plan_info_t(ctypes.Structure):

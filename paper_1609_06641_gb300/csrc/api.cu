@@ -21,6 +21,9 @@
 namespace chw {
 using LowpLaunchFn = cudaError_t (*)(const CUtensorMap*, const LowpArgs&, int64_t, cudaStream_t);
 LowpLaunchFn lookup_lowp(int m, bool f16, bool end);
+using RowstackLaunchFn = cudaError_t (*)(const CUtensorMap*, const FusedArgs&, uint32_t*, int64_t, int64_t,
+                                         cudaStream_t);
+RowstackLaunchFn lookup_rowstack(int m, int var);
 }  // namespace chw
 
 namespace {
@@ -43,7 +46,7 @@ chw_status_t fail(chw_status_t s, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(CHW_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
   } while (0)
 
-enum Tier { kTierSimple = 0, kTierFused = 1, kTierCluster = 2, kTierTwoPass = 3, kTierRagged = 4, kTierLowp = 5 };
+enum Tier { kTierSimple = 0, kTierFused = 1, kTierCluster = 2, kTierTwoPass = 3, kTierRagged = 4, kTierLowp = 5, kTierRowStack = 6 };
 
 struct Shape {
   int tb, cb;
@@ -137,6 +140,7 @@ struct chw_plan_s {
   int tier = kTierSimple;
   int passes = 1;
   int row_bits = 0;  // two-pass: b (pass 1 rows); a = m - b
+  int64_t rowstack_slots = 0;  // row-stack tier: scratch slots of 2^m words (one per CTA)
   int64_t total = 0;
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
@@ -250,6 +254,28 @@ chw_status_t launch_lowp_fused(chw_plan_s* p, const void* x, void* y, int64_t ba
   return CHW_OK;
 }
 
+// Row-stack tier: one CTA per signal, rows through an L2-resident scratch slot per CTA.
+chw_status_t launch_rowstack(chw_plan_s* p, const void* x, void* y, int64_t batch, const int8_t* diag_in,
+                             const int8_t* diag_out, void* ws, int64_t slots, cudaStream_t st) {
+  chw::RowstackLaunchFn fn = chw::lookup_rowstack(p->m, fused_variant(p, true));
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no row-stack kernel for m=%d", p->m);
+  CUtensorMap map;
+  const int64_t total = batch << p->m;
+  chw_status_t r = make_rows_map(&map, x, total, 14);
+  if (r != CHW_OK) return r;
+  chw::FusedArgs a{};
+  a.out = y;
+  a.out_total = total;
+  a.end_scale = end_scale_f32(p->m);
+  a.diag_in = diag_in;
+  a.diag_out = diag_out;
+  a.diag_mask = (int64_t{1} << p->m) - 1;
+  a.status = p->d_status;
+  const int64_t grid = batch < slots ? batch : slots;
+  CHW_CUDA(fn(&map, a, static_cast<uint32_t*>(ws), grid, batch, st));
+  return CHW_OK;
+}
+
 chw_status_t launch_simple(chw_plan_s* p, const void* x, void* y, int64_t batch, const int32_t* exp_in,
                            int32_t* exp_out, const int8_t* diag_in, const int8_t* diag_out, cudaStream_t st) {
   chw::SimpleArgs a{};
@@ -290,6 +316,8 @@ chw_status_t run_transform(chw_plan_s* p, const void* x, void* y, int64_t batch,
       return launch_simple(p, x, y, batch, exp_in, exp_out, diag_in, diag_out, st);
     case kTierLowp:
       return launch_lowp_fused(p, x, y, batch, exp_in, exp_out, diag_in, diag_out, st);
+    case kTierRowStack:
+      return launch_rowstack(p, x, y, batch, diag_in, diag_out, ws, p->rowstack_slots, st);
     case kTierFused:
     case kTierCluster:
       return launch_row_pass(p, m, 0, fused_variant(p, true), x, y, total, diag_in, diag_out, dmask, 0,
@@ -390,8 +418,10 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
   } else if (m <= 17) {
     if (m < 5 && p->total % 32 != 0) {
       p->tier = kTierSimple;
+    } else if (m >= 15) {
+      p->tier = (flags & CHW_FLAG_ROWSTACK) != 0 ? kTierRowStack : kTierCluster;
     } else {
-      p->tier = m >= 15 ? kTierCluster : kTierFused;
+      p->tier = kTierFused;
     }
   } else if (m <= 29) {
     p->tier = kTierTwoPass;
@@ -414,6 +444,20 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     return fail(CHW_ERR_CUDA, "cudaMalloc(status): %s", cudaGetErrorString(e));
   }
   cudaMemset(p->d_status, 0, sizeof(int));
+  if (p->tier == kTierRowStack) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    p->rowstack_slots = sms > 0 ? sms : 1;
+    if (p->rowstack_slots > batch) p->rowstack_slots = batch;
+    p->workspace_bytes = static_cast<size_t>(p->rowstack_slots << m) * elem_bytes(dtype);
+    e = cudaMalloc(&p->workspace, p->workspace_bytes);
+    if (e != cudaSuccess) {
+      cudaFree(p->d_status);
+      delete p;
+      cudaGetLastError();
+      return fail(CHW_ERR_OOM, "workspace of %zu bytes: %s", p->workspace_bytes, cudaGetErrorString(e));
+    }
+  }
   if (p->tier == kTierTwoPass) {
     p->workspace_bytes = static_cast<size_t>(p->total) * elem_bytes(dtype);
     e = cudaMalloc(&p->workspace, p->workspace_bytes);
@@ -521,6 +565,8 @@ chw_status_t chw_forward_host(chw_plan_t p, const void* x_host, void* y_host, co
       if (cudaStreamCreateWithFlags(&p->h_stream[i], cudaStreamNonBlocking) != cudaSuccess ||
           cudaMalloc(&p->h_buf[i], bytes) != cudaSuccess ||
           (p->tier == kTierTwoPass && cudaMalloc(&p->h_ws[i], bytes) != cudaSuccess) ||
+          (p->tier == kTierRowStack &&
+           cudaMalloc(&p->h_ws[i], static_cast<size_t>(p->rowstack_slots << p->m) * eb) != cudaSuccess) ||
           (lowp && (cudaMalloc(&p->h_exp[i][0], chunk * sizeof(int32_t)) != cudaSuccess ||
                     cudaMalloc(&p->h_exp[i][1], chunk * sizeof(int32_t)) != cudaSuccess))) {
         cudaGetLastError();

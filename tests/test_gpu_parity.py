@@ -57,7 +57,18 @@ def test_f32_every_m(chw, torch, m, norm):
     x = W.normal_f32(m, batch, seed=100 + m)
     info = _check_f32(chw, torch, x, m, norm)
     if m >= 15:
-        assert info.tier == 2 and info.cluster == 1 << (m - 14)
+        assert info.tier == 2 and info.cluster == 1 << (m - 14)  # thread-block cluster
+
+
+@pytest.mark.parametrize("m", [15, 16, 17])
+@pytest.mark.parametrize("norm", ["per_level", "end"])
+def test_rowstack_tier(chw, torch, m, norm):
+    x = W.normal_f32(m, 5, seed=150 + m)
+    info = _check_f32(chw, torch, x, m, norm, flags=4)
+    assert info.tier == 6  # one CTA per signal, rows through L2
+    xi = W.uniform_int32(m, 3, seed=160 + m, bound=2 ** (29 - m))
+    got, _ = run_forward(chw, torch, xi, m, "i32", "none", flags=4)
+    assert np.array_equal(got, O.wht_fast_dyadic(xi.astype(np.int64), m, normalised=False).astype(np.int32))
 
 
 @pytest.mark.parametrize("m", [0, 1, 2, 3, 4, 5, 7, 10, 12, 13, 14, 15, 16, 17])
