@@ -342,111 +342,13 @@ __device__ __forceinline__ void tile_issue(const CUtensorMap* tin, int in_row0, 
   for (int j = 0; j < NBOX; ++j) tma_load_2d(buf + j * BOXR * 32, tin, bar, 0, in_row0 + j * BOXR, pol);
 }
 
-// Transform the (cluster) tile held in `buf` once `bar` completes phase `parity`: the
-// input's first element is `in_elem0` (for the adjoint's diagonal) and the outputs start
-// at element `out_base`.  All threads of the CTA call this; it returns with the CTA's
-// output stores issued and `buf` no longer read by this CTA's threads (a barrier is still
-// needed before `buf` is refilled).
-template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
-__device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base, const FusedArgs& args,
-                                             uint32_t* buf, uint64_t* bar, uint32_t parity) {
+// Copy the staged tile (output order, staging swizzle) to global memory with coalesced
+// 16-byte stores; `out_base` is the element index of the (cluster) tile's first output.
+template <int TLO, int M, int TB, int CB, class BF, int OUTMODE>
+__device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, uint32_t rank, const FusedArgs& args) {
   using Cfg = FusedCfg<TLO, M, TB, CB>;
   constexpr FusedPlan F = Cfg::plan;
   constexpr int NT = 1 << (TB - 6);
-  constexpr int NR = 1 << CB;
-  constexpr uint32_t LMASK = Cfg::LMASK;
-  constexpr Phase P1 = F.p1, P2 = F.p2, P3 = F.p3, FW = F.fw;
-  constexpr Lin LS = F.lin_s, LB = F.lin_b, LF = F.lin_final;
-
-  const uint32_t tid = threadIdx.x;
-  const uint32_t lane = tid & 31u, warp = tid >> 5;
-  const uint32_t rank = CB > 0 ? cluster_ctarank() : 0u;
-  BF bf{};
-  if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
-
-  if (!mbar_wait_bounded(bar, parity, kWaitTries)) {
-    if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
-  }
-
-  uint32_t v[64];
-  auto scale_all = [&]() {
-    if constexpr (SCALE) {
-#pragma unroll
-      for (int k = 0; k < 64; ++k) v[k] = __float_as_uint(__fmul_rn(__uint_as_float(v[k]), args.end_scale));
-    }
-  };
-
-  if constexpr (F.has_p1) {
-    const uint32_t base = thread_pos<P1, LS, LMASK>(lane, warp, 0);
-    load_phase<P1, LS, LMASK>(v, buf, base);
-    if (args.diag_in != nullptr) {
-      const uint32_t tl = thread_label<P1>(lane, warp, 0);
-      sfor<64>([&](auto k) {
-        constexpr uint32_t kl = reg_label(P1, k);
-        const int64_t idx = in_elem0 + (tl | kl);
-        if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
-      });
-    }
-    butterflies<P1, 0, (TLO + M < 5 ? TLO + M : 5)>(v, bf);
-    if constexpr (F.p1_final) {
-      scale_all();
-      __syncthreads();
-      store_phase<FW, P1, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
-    } else {
-      store_phase<P1, P1, LS, LMASK>(v, buf, base);
-    }
-    __syncthreads();
-  }
-
-  if constexpr (!F.p1_final) {
-    const uint32_t base2 = thread_pos<P2, LS, LMASK>(lane, warp, 0);
-    load_phase<P2, LS, LMASK>(v, buf, base2);
-    butterflies<P2, (TLO > 5 ? TLO : 5), (TLO + M < 11 ? TLO + M : 11)>(v, bf);
-    if constexpr (F.p2_final) {
-      scale_all();
-      __syncthreads();
-      store_phase<FW, P2, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
-      __syncthreads();
-    } else if constexpr (CB > 0) {
-      // Cluster exchange: push each value to the CTA that finishes it (16-byte DSMEM
-      // stores, fire and forget), then phase 3 reads only local shared memory.
-      constexpr Phase P2W = F.p2w;
-      constexpr Lin LR = F.lin_r;
-      cluster_arrive();  // every CTA has read its tile (the pushes overwrite it)
-      cluster_wait();
-      {
-        const uint32_t tl = thread_label<P2>(lane, warp, 0) | (rank << TB);
-        uint32_t dest = 0;
-#pragma unroll
-        for (int i = 0; i < CB; ++i) dest |= ((tl >> P3.cta[i]) & 1u) << i;
-        uint32_t base = 0;
-#pragma unroll
-        for (int b = 0; b < TB + CB; ++b)
-          if ((tl >> b) & 1u) base ^= LR.img[b];
-        store_phase_remote<P2W, P2, LR>(v, mapa_shared(smem_u32(buf), dest), base);
-      }
-      cluster_arrive();  // the pushes are visible cluster-wide
-      cluster_wait();
-      load_phase<P3, LR, ~0u>(v, buf, thread_pos<P3, LR, ~0u>(lane, warp, rank));
-      butterflies<P3, 11, TLO + M>(v, bf);
-      scale_all();
-      __syncthreads();
-      store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, rank));
-      __syncthreads();
-    } else {
-      if constexpr (!F.b_is_s) __syncthreads();
-      store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
-      __syncthreads();
-      load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, rank));
-      butterflies<P3, 11, TLO + M>(v, bf);
-      scale_all();
-      __syncthreads();
-      store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, rank));
-      __syncthreads();
-    }
-  }
-
-  // ---- copy-out: coalesced 16-byte stores of the staged tile
   if constexpr (CB > 0) {
     uint32_t ro = 0;
 #pragma unroll
@@ -457,7 +359,7 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
   constexpr int NCH = 1 << (TB - 2);
   constexpr int S = F.stage_s;
 #pragma unroll 4
-  for (int c = tid; c < NCH; c += NT) {
+  for (int c = threadIdx.x; c < NCH; c += NT) {
     const uint32_t o = static_cast<uint32_t>(c) << 2;
     const uint32_t pos = o ^ (((o >> S) & 7u) << 2);
     uint4 q = *reinterpret_cast<const uint4*>(buf + pos);
@@ -494,6 +396,158 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
   }
 }
 
+// Phases 1 and 2 of a tile in `buf` (TMA complete): on return v holds phase 2's values and
+// no thread reads `buf` any more once the caller has synchronised.  Only for tiles that
+// have a third phase.
+template <int TLO, int M, int TB, int CB, class BF>
+__device__ __forceinline__ void phases_1_2(uint32_t (&v)[64], int64_t in_elem0, const FusedArgs& args, uint32_t* buf,
+                                           const BF& bf) {
+  using Cfg = FusedCfg<TLO, M, TB, CB>;
+  constexpr FusedPlan F = Cfg::plan;
+  static_assert(F.has_p3, "tiles with a third phase");
+  constexpr uint32_t LMASK = Cfg::LMASK;
+  constexpr Phase P1 = F.p1, P2 = F.p2;
+  constexpr Lin LS = F.lin_s;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if constexpr (F.has_p1) {
+    const uint32_t base = thread_pos<P1, LS, LMASK>(lane, warp, 0);
+    load_phase<P1, LS, LMASK>(v, buf, base);
+    if (args.diag_in != nullptr) {
+      const uint32_t tl = thread_label<P1>(lane, warp, 0);
+      sfor<64>([&](auto k) {
+        constexpr uint32_t kl = reg_label(P1, k);
+        const int64_t idx = in_elem0 + (tl | kl);
+        if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
+      });
+    }
+    butterflies<P1, 0, 5>(v, bf);
+    store_phase<P1, P1, LS, LMASK>(v, buf, base);
+    __syncthreads();
+  }
+  load_phase<P2, LS, LMASK>(v, buf, thread_pos<P2, LS, LMASK>(lane, warp, 0));
+  butterflies<P2, (TLO > 5 ? TLO : 5), 11>(v, bf);
+}
+
+// Push phase 2's values of a cluster tile to the CTAs that finish them (16-byte DSMEM
+// stores into their `buf`, receive layout lin_r).
+template <int TLO, int M, int TB, int CB>
+__device__ __forceinline__ void push_to_finishers(const uint32_t (&v)[64], uint32_t* buf, uint32_t rank) {
+  constexpr FusedPlan F = FusedCfg<TLO, M, TB, CB>::plan;
+  constexpr Phase P2 = F.p2, P2W = F.p2w, P3 = F.p3;
+  constexpr Lin LR = F.lin_r;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t tl = thread_label<P2>(lane, warp, 0) | (rank << TB);
+  uint32_t dest = 0;
+#pragma unroll
+  for (int i = 0; i < CB; ++i) dest |= ((tl >> P3.cta[i]) & 1u) << i;
+  uint32_t base = 0;
+#pragma unroll
+  for (int b = 0; b < TB + CB; ++b)
+    if ((tl >> b) & 1u) base ^= LR.img[b];
+  store_phase_remote<P2W, P2, LR>(v, mapa_shared(smem_u32(buf), dest), base);
+}
+
+// Phase 3 of a cluster tile from the local receive layout, then staging and copy-out.
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
+__device__ __forceinline__ void phase_3_out(int64_t out_base, const FusedArgs& args, uint32_t* buf, uint32_t rank,
+                                            const BF& bf) {
+  constexpr FusedPlan F = FusedCfg<TLO, M, TB, CB>::plan;
+  constexpr Phase P3 = F.p3, FW = F.fw;
+  constexpr Lin LR = F.lin_r, LF = F.lin_final;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t v[64];
+  load_phase<P3, LR, ~0u>(v, buf, thread_pos<P3, LR, ~0u>(lane, warp, rank));
+  butterflies<P3, 11, TLO + M>(v, bf);
+  if constexpr (SCALE) {
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = __float_as_uint(__fmul_rn(__uint_as_float(v[k]), args.end_scale));
+  }
+  __syncthreads();
+  store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, rank));
+  __syncthreads();
+  copy_out<TLO, M, TB, CB, BF, OUTMODE>(buf, out_base, rank, args);
+}
+
+// Transform the tile held in `buf` (one CTA, no cluster) once `bar` completes phase
+// `parity`: the input's first element is `in_elem0` (for the adjoint's diagonal) and the
+// outputs start at element `out_base`.  All threads of the CTA call this; it returns with
+// the CTA's output stores issued (a barrier is still needed before `buf` is refilled).
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
+__device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base, const FusedArgs& args,
+                                             uint32_t* buf, uint64_t* bar, uint32_t parity) {
+  static_assert(CB == 0, "cluster tiles run in the pipelined cluster kernel");
+  using Cfg = FusedCfg<TLO, M, TB, CB>;
+  constexpr FusedPlan F = Cfg::plan;
+  constexpr uint32_t LMASK = Cfg::LMASK;
+  constexpr Phase P1 = F.p1, P2 = F.p2, P3 = F.p3, FW = F.fw;
+  constexpr Lin LS = F.lin_s, LB = F.lin_b, LF = F.lin_final;
+
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
+  BF bf{};
+  if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
+
+  if (!mbar_wait_bounded(bar, parity, kWaitTries)) {
+    if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+  }
+
+  uint32_t v[64];
+  auto scale_all = [&]() {
+    if constexpr (SCALE) {
+#pragma unroll
+      for (int k = 0; k < 64; ++k) v[k] = __float_as_uint(__fmul_rn(__uint_as_float(v[k]), args.end_scale));
+    }
+  };
+
+  if constexpr (F.has_p3) {
+    phases_1_2<TLO, M, TB, CB, BF>(v, in_elem0, args, buf, bf);
+    if constexpr (!F.b_is_s) __syncthreads();
+    store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
+    __syncthreads();
+    load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, 0));
+    butterflies<P3, 11, TLO + M>(v, bf);
+    scale_all();
+    __syncthreads();
+    store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
+    __syncthreads();
+  } else if constexpr (F.has_p1) {
+    const uint32_t base = thread_pos<P1, LS, LMASK>(lane, warp, 0);
+    load_phase<P1, LS, LMASK>(v, buf, base);
+    if (args.diag_in != nullptr) {
+      const uint32_t tl = thread_label<P1>(lane, warp, 0);
+      sfor<64>([&](auto k) {
+        constexpr uint32_t kl = reg_label(P1, k);
+        const int64_t idx = in_elem0 + (tl | kl);
+        if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
+      });
+    }
+    butterflies<P1, 0, (TLO + M < 5 ? TLO + M : 5)>(v, bf);
+    if constexpr (F.p1_final) {
+      scale_all();
+      __syncthreads();
+      store_phase<FW, P1, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
+      __syncthreads();
+    } else {
+      store_phase<P1, P1, LS, LMASK>(v, buf, base);
+      __syncthreads();
+      load_phase<P2, LS, LMASK>(v, buf, thread_pos<P2, LS, LMASK>(lane, warp, 0));
+      butterflies<P2, 5, TLO + M>(v, bf);
+      scale_all();
+      __syncthreads();
+      store_phase<FW, P2, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
+      __syncthreads();
+    }
+  } else {
+    load_phase<P2, LS, LMASK>(v, buf, thread_pos<P2, LS, LMASK>(lane, warp, 0));
+    butterflies<P2, (TLO > 5 ? TLO : 5), TLO + M>(v, bf);
+    scale_all();
+    __syncthreads();
+    store_phase<FW, P2, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
+    __syncthreads();
+  }
+  copy_out<TLO, M, TB, CB, BF, OUTMODE>(buf, out_base, 0, args);
+}
+
 // Load + transform one tile (the persistent ragged kernel's form: no prefetch).
 template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
 __device__ __forceinline__ void fused_tile(const CUtensorMap* tin, int in_row0, int64_t out_base,
@@ -516,12 +570,13 @@ constexpr int fused_ctas_per_sm() {
 }
 
 // ------------------------------------------------------------------ the batched kernel
-// Persistent: each CTA (cluster) walks the units u = first, first + stride, ... with two
-// shared buffers; the TMA load of unit k+1 is issued before unit k is transformed, so HBM
-// reads overlap the butterflies and the stores of the previous unit.
+// Persistent: each CTA walks the units u = first, first + stride, ... with two shared
+// buffers; the TMA load of unit k+1 is issued before unit k is transformed, so HBM reads
+// overlap the butterflies and the stores of the previous unit.
 template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
 __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
     fused_kernel(const __grid_constant__ CUtensorMap tin, const FusedArgs args, const int64_t units) {
+  static_assert(CB == 0, "cluster shapes use cluster_kernel");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   uint32_t* buf0 = reinterpret_cast<uint32_t*>(base);
@@ -533,11 +588,9 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
     fence_mbar_init();
   }
   __syncthreads();
-  const uint32_t rank = CB > 0 ? cluster_ctarank() : 0u;
-  const int64_t stride = gridDim.x >> CB;
-  const int64_t first = blockIdx.x >> CB;
-  // input rows of unit u for this CTA (a cluster's CTAs split a unit into 2^CB slices)
-  auto row0 = [&](int64_t u) { return static_cast<int>(((u << CB) | rank) << (TB - 5)); };
+  const int64_t stride = gridDim.x;
+  const int64_t first = blockIdx.x;
+  auto row0 = [&](int64_t u) { return static_cast<int>(u << (TB - 5)); };
   if (threadIdx.x == 0 && first < units) tile_issue<TB>(&tin, row0(first), buf0, bar);
   int k = 0;
   for (int64_t u = first; u < units; u += stride, ++k) {
@@ -545,11 +598,94 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
     uint32_t* nxt = (k & 1) ? buf0 : buf1;
     const int64_t un = u + stride;
     if (threadIdx.x == 0 && un < units) tile_issue<TB>(&tin, row0(un), nxt, bar + ((k + 1) & 1));
-    const int64_t out_base = CB > 0 ? (u << (TB + CB)) : (u << TB);
-    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(static_cast<int64_t>(row0(u)) * 32, out_base, args, cur,
+    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(static_cast<int64_t>(row0(u)) * 32, u << TB, args, cur,
                                                      bar + (k & 1), (k >> 1) & 1);
     __syncthreads();
   }
+}
+
+// ------------------------------------------------------------------ the cluster kernel
+// A cluster of 2^CB CTAs owns one unit (a 2^(TB+CB)-element tile) at a time and walks its
+// units persistently with three shared buffers per CTA.  Iteration k: prefetch unit k+1,
+// run phases 1-2 of unit k, tell every CTA "my buffer of unit k has been read" (free), wait
+// until all have said so, push phase 2's values into the finishing CTAs' buffers, tell
+// them "pushed" (full); then finish unit k-1 (its pushes arrived an iteration earlier):
+// phase 3 from the local buffer, staging, copy-out.  The signals are mbarrier arrivals on
+// peer CTAs with release/acquire at cluster scope; every wait is bounded.
+constexpr int kClusterBufs = 3;
+
+template <int TB>
+constexpr int cluster_smem_bytes() {
+  return kClusterBufs * (4 << TB) + 1024 + 128;
+}
+
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
+__global__ void __launch_bounds__(1 << (TB - 6), 1)
+    cluster_kernel(const __grid_constant__ CUtensorMap tin, const FusedArgs args, const int64_t units) {
+  static_assert(CB > 0, "cluster shapes only");
+  constexpr int NR = 1 << CB;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  uint32_t* bufs = reinterpret_cast<uint32_t*>(base);
+  uint64_t* tma = reinterpret_cast<uint64_t*>(base + kClusterBufs * (4u << TB));
+  uint64_t* freeb = tma + kClusterBufs;
+  uint64_t* fullb = freeb + kClusterBufs;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u;
+  if (tid == 0) {
+    for (int i = 0; i < kClusterBufs; ++i) {
+      mbar_init(tma + i, 1);
+      mbar_init(freeb + i, NR);
+      mbar_init(fullb + i, NR);
+    }
+    fence_mbar_init();
+  }
+  cluster_arrive();  // every CTA's barriers exist before any peer signals them
+  cluster_wait();
+  const uint32_t rank = cluster_ctarank();
+  const int64_t stride = gridDim.x >> CB;
+  const int64_t first = blockIdx.x >> CB;
+  const int64_t K = first < units ? (units - first + stride - 1) / stride : 0;
+  auto buf_of = [&](int64_t k) { return bufs + (k % kClusterBufs) * (int64_t{1} << TB); };
+  auto row0 = [&](int64_t k) { return static_cast<int>((((first + k * stride) << CB) | rank) << (TB - 5)); };
+  BF bf{};
+  if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
+  auto timeout = [&]() {
+    if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+  };
+
+  if (tid == 0 && K > 0) tile_issue<TB>(&tin, row0(0), buf_of(0), tma);
+  for (int64_t k = 0; k <= K; ++k) {
+    if (k < K) {
+      const int b = static_cast<int>(k % kClusterBufs);
+      const uint32_t par = static_cast<uint32_t>((k / kClusterBufs) & 1);
+      if (tid == 0 && k + 1 < K) {
+        const int b1 = static_cast<int>((k + 1) % kClusterBufs);
+        tile_issue<TB>(&tin, row0(k + 1), buf_of(k + 1), tma + b1);
+      }
+      if (!mbar_wait_bounded(tma + b, par, kWaitTries)) timeout();
+      uint32_t v[64];
+      phases_1_2<TLO, M, TB, CB, BF>(v, static_cast<int64_t>(row0(k)) * 32, args, buf_of(k), bf);
+      __syncthreads();  // this CTA no longer reads buffer b of unit k
+      if (tid < NR) mbar_remote_arrive(freeb + b, tid);
+      if (!mbar_wait_cluster_bounded(freeb + b, par, kWaitTries)) timeout();
+      push_to_finishers<TLO, M, TB, CB>(v, buf_of(k), rank);
+      __syncthreads();  // every push of this CTA is issued
+      if (tid < NR) {
+        fence_acq_rel_cluster();
+        mbar_remote_arrive(fullb + b, tid);
+      }
+    }
+    if (k >= 1) {
+      const int64_t kp = k - 1;
+      const int b = static_cast<int>(kp % kClusterBufs);
+      const uint32_t par = static_cast<uint32_t>((kp / kClusterBufs) & 1);
+      if (!mbar_wait_cluster_bounded(fullb + b, par, kWaitTries)) timeout();
+      phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>((first + kp * stride) << (TB + CB), args, buf_of(kp), rank, bf);
+    }
+    __syncthreads();
+  }
+  cluster_arrive();  // no CTA leaves while a peer may still push into it or signal it
+  cluster_wait();
 }
 
 }  // namespace chw

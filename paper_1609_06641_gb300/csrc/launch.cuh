@@ -54,8 +54,13 @@ int64_t persistent_cap_override();  // CHW_MAX_RESIDENT_UNITS, 0 = none (tuning)
 
 template <int TLO, int M, int TB, int CB, class BF, bool SC, int OM>
 cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t units, cudaStream_t st) {
-  auto kern = fused_kernel<TLO, M, TB, CB, BF, SC, OM>;
-  constexpr int smem = fused_smem_bytes<TB>();
+  constexpr auto kern = [] {
+    if constexpr (CB > 0)
+      return cluster_kernel<TLO, M, TB, CB, BF, SC, OM>;
+    else
+      return fused_kernel<TLO, M, TB, CB, BF, SC, OM>;
+  }();
+  constexpr int smem = CB > 0 ? cluster_smem_bytes<TB>() : fused_smem_bytes<TB>();
   constexpr int threads = 1 << (TB - 6);
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (attr != cudaSuccess) return attr;
