@@ -606,12 +606,17 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
 
 // ------------------------------------------------------------------ the cluster kernel
 // A cluster of 2^CB CTAs owns one unit (a 2^(TB+CB)-element tile) at a time and walks its
-// units persistently with three shared buffers per CTA.  Iteration k: prefetch unit k+1,
-// run phases 1-2 of unit k, tell every CTA "my buffer of unit k has been read" (free), wait
-// until all have said so, push phase 2's values into the finishing CTAs' buffers, tell
-// them "pushed" (full); then finish unit k-1 (its pushes arrived an iteration earlier):
-// phase 3 from the local buffer, staging, copy-out.  The signals are mbarrier arrivals on
-// peer CTAs with release/acquire at cluster scope; every wait is bounded.
+// units persistently with three shared buffers per CTA, rotating roles:
+//   unit u's input S_u is loaded by TMA into buffer u mod 3;
+//   phases 1-2 of unit u read it, after which it receives the pushes R_{u+1} of unit u+1;
+//   phase 3, staging and copy-out of unit u+1 then use it, and the TMA load of unit u+3
+//   refills it.
+// Iteration k: finish unit k-1 (wait "full" for R_{k-1}, phase 3, staging, copy-out),
+// issue the TMA load of unit k+1 into the buffer that just became free, then run phases
+// 1-2 of unit k, signal every CTA that this buffer may now receive R_{k+1} ("free"), wait
+// until every CTA's buffer for R_k is free (signalled an iteration earlier), push, and
+// signal "full" for R_k.  Signals are remote mbarrier arrivals with release/acquire at
+// cluster scope; every wait is bounded.
 constexpr int kClusterBufs = 3;
 
 template <int TB>
@@ -628,8 +633,8 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
   uint8_t* base = align1024(smem_raw);
   uint32_t* bufs = reinterpret_cast<uint32_t*>(base);
   uint64_t* tma = reinterpret_cast<uint64_t*>(base + kClusterBufs * (4u << TB));
-  uint64_t* freeb = tma + kClusterBufs;
-  uint64_t* fullb = freeb + kClusterBufs;
+  uint64_t* freeb = tma + kClusterBufs;    // freeb[u % 3]: every CTA's buffer for R_u is free
+  uint64_t* fullb = freeb + kClusterBufs;  // fullb[u % 3]: every CTA has pushed R_u here
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
   if (tid == 0) {
     for (int i = 0; i < kClusterBufs; ++i) {
@@ -645,44 +650,42 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
   const int64_t stride = gridDim.x >> CB;
   const int64_t first = blockIdx.x >> CB;
   const int64_t K = first < units ? (units - first + stride - 1) / stride : 0;
-  auto buf_of = [&](int64_t k) { return bufs + (k % kClusterBufs) * (int64_t{1} << TB); };
+  auto buf = [&](int64_t i) { return bufs + (i % kClusterBufs) * (int64_t{1} << TB); };  // S_i; R_{i+1}
   auto row0 = [&](int64_t k) { return static_cast<int>((((first + k * stride) << CB) | rank) << (TB - 5)); };
+  auto par = [](int64_t u) { return static_cast<uint32_t>((u / kClusterBufs) & 1); };
   BF bf{};
   if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
   auto timeout = [&]() {
     if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
   };
 
-  if (tid == 0 && K > 0) tile_issue<TB>(&tin, row0(0), buf_of(0), tma);
+  if (tid == 0 && K > 0) tile_issue<TB>(&tin, row0(0), buf(0), tma);
+  if (tid == 0 && K > 1) tile_issue<TB>(&tin, row0(1), buf(1), tma + 1);
+  if (tid < NR && K > 0) mbar_remote_arrive(freeb + 0, tid);  // buffer 2 (R_0) starts free
   for (int64_t k = 0; k <= K; ++k) {
+    if (k >= 1) {
+      // ---- finish unit k-1: its pushes R_{k-1} sit in buffer (k-2) mod 3
+      const int64_t u = k - 1;
+      if (!mbar_wait_cluster_bounded(fullb + u % kClusterBufs, par(u), kWaitTries)) timeout();
+      phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>((first + u * stride) << (TB + CB), args, buf(u + 2), rank, bf);
+      __syncthreads();  // buffer (k+1) mod 3 is free: the copy-out has read it
+      if (tid == 0 && k + 1 < K) tile_issue<TB>(&tin, row0(k + 1), buf(k + 1), tma + (k + 1) % kClusterBufs);
+    }
     if (k < K) {
-      const int b = static_cast<int>(k % kClusterBufs);
-      const uint32_t par = static_cast<uint32_t>((k / kClusterBufs) & 1);
-      if (tid == 0 && k + 1 < K) {
-        const int b1 = static_cast<int>((k + 1) % kClusterBufs);
-        tile_issue<TB>(&tin, row0(k + 1), buf_of(k + 1), tma + b1);
-      }
-      if (!mbar_wait_bounded(tma + b, par, kWaitTries)) timeout();
+      // ---- phases 1-2 of unit k, then push R_k
+      if (!mbar_wait_bounded(tma + k % kClusterBufs, par(k), kWaitTries)) timeout();
       uint32_t v[64];
-      phases_1_2<TLO, M, TB, CB, BF>(v, static_cast<int64_t>(row0(k)) * 32, args, buf_of(k), bf);
-      __syncthreads();  // this CTA no longer reads buffer b of unit k
-      if (tid < NR) mbar_remote_arrive(freeb + b, tid);
-      if (!mbar_wait_cluster_bounded(freeb + b, par, kWaitTries)) timeout();
-      push_to_finishers<TLO, M, TB, CB>(v, buf_of(k), rank);
+      phases_1_2<TLO, M, TB, CB, BF>(v, static_cast<int64_t>(row0(k)) * 32, args, buf(k), bf);
+      __syncthreads();  // buffer k mod 3 is no longer read: it may receive R_{k+1}
+      if (tid < NR) mbar_remote_arrive(freeb + (k + 1) % kClusterBufs, tid);
+      if (!mbar_wait_cluster_bounded(freeb + k % kClusterBufs, par(k), kWaitTries)) timeout();
+      push_to_finishers<TLO, M, TB, CB>(v, buf(k + 2), rank);
       __syncthreads();  // every push of this CTA is issued
       if (tid < NR) {
         fence_acq_rel_cluster();
-        mbar_remote_arrive(fullb + b, tid);
+        mbar_remote_arrive(fullb + k % kClusterBufs, tid);
       }
     }
-    if (k >= 1) {
-      const int64_t kp = k - 1;
-      const int b = static_cast<int>(kp % kClusterBufs);
-      const uint32_t par = static_cast<uint32_t>((kp / kClusterBufs) & 1);
-      if (!mbar_wait_cluster_bounded(fullb + b, par, kWaitTries)) timeout();
-      phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>((first + kp * stride) << (TB + CB), args, buf_of(kp), rank, bf);
-    }
-    __syncthreads();
   }
   cluster_arrive();  // no CTA leaves while a peer may still push into it or signal it
   cluster_wait();
