@@ -460,9 +460,9 @@ def main():
             "peak": peak,
             "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": traffic_from_profile("fused_m16_cluster4_end"),
+            "traffic": traffic_from_profile(f"m{m}_b{batch}_f32_end_tier{info.tier}"),
             "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else "fallback",
-            "kernel": {2: "fused_kernel (4-CTA cluster per signal, DSMEM exchange)",
+            "kernel": {2: "cluster_kernel<0,16,14,2> (4-CTA cluster per signal, DSMEM exchange)",
                        6: "rowstack_kernel<16> (one CTA per signal, rows through L2)"}.get(info.tier, str(info.tier)),
         },
         "e2e": {
