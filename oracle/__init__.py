@@ -19,6 +19,8 @@ Walsh-Hadamard Transform", arXiv 1609.06641):
   cascade of Theorem 1 taken literally in stage order (O4, any dtype, with an
   operation counter for Lemma 1 / Theorem 2) and its transpose, the reversed
   cascade of inverse Haar transforms.
+* ``wavelets``     -- the Haar transform Psi_m of eq. (2), its transpose, and the
+  Haar-Walsh transform H_m Psi_m^T of eq. (4) (stages 1..m-1 of Theorem 1).
 * ``lowp``         -- the bf16/fp16 storage form: per-signal power-of-two
   exponents decided in fp32, the same precision the kernels decide them in.
 * ``errors``       -- FP64 normwise relative error per signal.
@@ -48,6 +50,7 @@ from .transforms import (
     end_scale_f32,
     inv_sqrt2,
 )
+from .wavelets import haar_forward, haar_inverse, haar_levels, haar_walsh
 from .lowp import codes_to_f32, dequantise, lowp_forward_reference, round_to_bf16, round_to_f16
 from .errors import rel_err_per_signal
 
@@ -69,6 +72,10 @@ __all__ = [
     "OpCounter",
     "end_scale_f32",
     "inv_sqrt2",
+    "haar_forward",
+    "haar_inverse",
+    "haar_levels",
+    "haar_walsh",
     "lowp_forward_reference",
     "round_to_bf16",
     "round_to_f16",
