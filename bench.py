@@ -188,7 +188,7 @@ def traffic_from_profile(kernel_key):
         return None
     from paper_1609_06641_gb300 import build
 
-    if ent.get("build_digest") != build._digest():
+    if ent.get("kernel_digest") != build.kernel_digest():
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -338,6 +338,22 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     ms = time_device(lambda: chw.chw_adjoint(pd, yd, xd, diag=d), k, warmup, 1, st)
     rec("m14_b512_DH_adjoint", 2 * xd.numel() * 4, ms, 1)
     del xd, yd
+    # Haar transform (eq. (2)), its transpose, Haar-Walsh (eq. (4)) and the forward with its
+    # Haar side output, on the headline shape
+    xh = torch.randn(BATCH, 1 << M, device=dev, generator=g)
+    zh = torch.empty_like(xh)
+    yh = torch.empty_like(xh)
+    ph = chw.chw_plan(M, BATCH, "f32", "per_level", chw.CHW_FLAG_HAAR_WALSH)
+    nb = xh.numel() * 4
+    ms = time_device(lambda: chw.chw_haar(ph, xh, zh), k, warmup, 1, st)
+    rec("m16_b4096_f32_haar", 2 * nb, ms, 2)
+    ms = time_device(lambda: chw.chw_haar_inverse(ph, zh, yh), k, warmup, 1, st)
+    rec("m16_b4096_f32_haar_inverse", 2 * nb, ms, 2)
+    ms = time_device(lambda: chw.chw_from_haar(ph, zh, yh), k, warmup, 1, st)
+    rec("m16_b4096_f32_haar_walsh", 2 * nb, ms, 1)
+    ms = time_device(lambda: chw.chw_forward_haar(ph, xh, yh, zh), k, warmup, 1, st)
+    rec("m16_b4096_f32_forward_with_haar_output", 3 * nb, ms, 3)
+    del xh, zh, yh, ph
     # ragged: 10,000 signals with m uniform on 6..20 (seed 5), one graph launch
     from paper_1609_06641_gb300 import workloads as W
 

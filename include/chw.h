@@ -26,7 +26,9 @@
  *     the boundary.  chw_last_error_message() gives a one-line reason (per host thread).
  *     Errors found on the device (a bounded wait that ran out, a checked-mode index
  *     fault) are latched in the plan and reported by chw_last_device_status().
- *   - In-place operation (x == y) is allowed for every call.
+ *   - In-place operation (x == y) is allowed for every call except the Haar transforms
+ *     (chw_haar, chw_haar_inverse, chw_forward_haar), whose input and output must not
+ *     overlap.
  */
 #ifndef CHW_H
 #define CHW_H
@@ -71,6 +73,7 @@ typedef enum chw_norm_e {
 #define CHW_FLAG_FORCE_MULTIPASS 2u /* split m into two HBM passes even if one fits     */
 #define CHW_FLAG_ROWSTACK 4u        /* m = 15..17: one CTA per signal with its rows through */
                                     /* L2 instead of a thread-block cluster (DSMEM)        */
+#define CHW_FLAG_HAAR_WALSH 8u      /* also prepare chw_from_haar / chw_forward_haar       */
 
 typedef struct chw_plan_s* chw_plan_t;
 
@@ -150,6 +153,52 @@ chw_status_t chw_adjoint(chw_plan_t plan, const void* y, void* x, const int32_t*
 
 /* chw_forward_ragged -- transform every signal of a ragged plan (packed layout above). */
 chw_status_t chw_forward_ragged(chw_plan_t plan, const void* x, void* y, void* stream);
+
+/*
+ * Haar wavelet transforms.  A plan made by chw_plan (dtype CHW_F32 or CHW_I32, any m) also
+ * runs the Haar transform Psi_m of eq. (2), its transpose, and the Haar-Walsh transform
+ * H_m Psi_m^T of eq. (4), on the same `batch` signals of 2^m elements.
+ *
+ * Haar layout (what eq. (2) produces): z = Psi_m x holds, per signal,
+ *   z[0]                          the approximation after all m levels,
+ *   z[2^{m-l} .. 2^{m-l+1} - 1]   the 2^{m-l} details of level l = 1..m,
+ * where level l maps the current approximation v (2^{m-l+1} values) to pair sums
+ * v_{2i} + v_{2i+1} (the next approximation) and differences v_{2i} - v_{2i+1}.
+ *
+ * Normalisation (the plan's norm): PER_LEVEL multiplies every butterfly output by
+ * fp32(1/sqrt2) (Psi_m exactly as eq. (2) scales it); NONE leaves the butterflies unscaled
+ * (int32: exact unnormalised Haar with two's-complement wrap); END leaves them unscaled
+ * and multiplies each coefficient once by fp32(2^{-L/2}), where L is the number of levels
+ * behind it (m for z[0], l for a level-l detail) -- after the butterflies for chw_haar,
+ * before them for chw_haar_inverse.
+ *
+ * chw_haar          z = Psi_m x.  x and z must not overlap.
+ * chw_haar_inverse  x = Psi_m^T z (= Psi_m^{-1} z for PER_LEVEL and END), the synthesis
+ *                   butterflies v_{2i} = u_i + d_i, v_{2i+1} = u_i - d_i from coarse to
+ *                   fine.  z and x must not overlap.
+ * Both read their input once and write their output once (plus 2^{-13} of the data in
+ * plan-owned scratch when m > 13); errors as for chw_forward.
+ */
+chw_status_t chw_haar(chw_plan_t plan, const void* x, void* z, void* stream);
+chw_status_t chw_haar_inverse(chw_plan_t plan, const void* z, void* x, void* stream);
+
+/*
+ * chw_from_haar -- the Haar-Walsh transform y = H_m Psi_m^T z of eq. (4): Haar
+ * coefficients z (layout above) to Walsh-Hadamard coefficients in dyadic order.  These are
+ * stages r = 1..m-1 of Theorem 1; by eq. (4) they act on each Haar scale separately, the
+ * level-l details (2^k values, k = m - l) going through H_k and z[0] through 1, so the
+ * call runs all scales of all signals as one ragged task set (scales of more than 2^20
+ * elements as separate two-pass transforms).  With PER_LEVEL or NONE the result equals
+ * chw_forward(x) bit for bit when z = chw_haar(x); with END each scale k is scaled once by
+ * fp32(2^{-k/2}).  In-place (z == y) allowed.  The plan must have been made with
+ * CHW_FLAG_HAAR_WALSH (which builds the task set); otherwise CHW_ERR_INVALID_ARG.
+ *
+ * chw_forward_haar -- y = H_m x together with its Haar side output z = Psi_m x: the CHW
+ * algorithm run as its two parts, stage 0 (chw_haar into z) and stages 1..m-1
+ * (chw_from_haar from z into y).  z must not overlap x or y.  Needs CHW_FLAG_HAAR_WALSH.
+ */
+chw_status_t chw_from_haar(chw_plan_t plan, const void* z, void* y, void* stream);
+chw_status_t chw_forward_haar(chw_plan_t plan, const void* x, void* y, void* z, void* stream);
 
 /*
  * chw_forward_host -- chw_forward for HOST buffers: copies x_host to the device, runs

@@ -1,7 +1,7 @@
 """GB300 (sm_103a) Cascading Haar Wavelet Walsh-Hadamard transform.
 
 Python side of the C ABI in include/chw.h.  The functions keep the C names (``chw_plan``,
-``chw_forward``, ``chw_adjoint``, ``chw_forward_ragged``, ...) and only marshal
+``chw_forward``, ``chw_adjoint``, ``chw_forward_ragged``, ``chw_haar``, ``chw_from_haar``, ...) and only marshal
 arguments: tensors must already live on the GPU (PyTorch is used for device memory and
 streams), and every step of the transform runs in the library's CUDA kernels.  There is
 no CPU fallback; a missing library raises.
@@ -19,6 +19,7 @@ from ._lib import (
     CHW_BF16,
     CHW_F16,
     CHW_F32,
+    CHW_FLAG_HAAR_WALSH,
     CHW_FLAG_ROWSTACK,
     CHW_FLAG_FORCE_MULTIPASS,
     CHW_FLAG_FORCE_SIMPLE,
@@ -187,6 +188,51 @@ def chw_forward_ragged(plan, x, y, stream=None):
     _check_data(x, plan, "x", total)
     _check_data(y, plan, "y", total)
     _lib.check(_lib.load().chw_forward_ragged(plan.handle, _ptr(x), _ptr(y), _stream(stream)), "chw_forward_ragged")
+    return y
+
+
+def _check_batched(plan, where):
+    if plan.m < 0:
+        raise ValueError(f"{where} takes a batched plan, not a ragged one")
+
+
+def chw_haar(plan, x, z, stream=None):
+    """z = Psi_m x, the Haar transform of eq. (2) (layout in chw.h); x and z must not overlap."""
+    _check_batched(plan, "chw_haar")
+    n = plan.batch << plan.m
+    _check_data(x, plan, "x", n)
+    _check_data(z, plan, "z", n)
+    _lib.check(_lib.load().chw_haar(plan.handle, _ptr(x), _ptr(z), _stream(stream)), "chw_haar")
+    return z
+
+
+def chw_haar_inverse(plan, z, x, stream=None):
+    """x = Psi_m^T z; z and x must not overlap."""
+    _check_batched(plan, "chw_haar_inverse")
+    n = plan.batch << plan.m
+    _check_data(z, plan, "z", n)
+    _check_data(x, plan, "x", n)
+    _lib.check(_lib.load().chw_haar_inverse(plan.handle, _ptr(z), _ptr(x), _stream(stream)), "chw_haar_inverse")
+    return x
+
+
+def chw_from_haar(plan, z, y, stream=None):
+    """y = H_m Psi_m^T z, the Haar-Walsh transform of eq. (4) (plan needs CHW_FLAG_HAAR_WALSH)."""
+    _check_batched(plan, "chw_from_haar")
+    n = plan.batch << plan.m
+    _check_data(z, plan, "z", n)
+    _check_data(y, plan, "y", n)
+    _lib.check(_lib.load().chw_from_haar(plan.handle, _ptr(z), _ptr(y), _stream(stream)), "chw_from_haar")
+    return y
+
+
+def chw_forward_haar(plan, x, y, z, stream=None):
+    """y = H_m x with the Haar side output z = Psi_m x (plan needs CHW_FLAG_HAAR_WALSH)."""
+    _check_batched(plan, "chw_forward_haar")
+    n = plan.batch << plan.m
+    for name, t in (("x", x), ("y", y), ("z", z)):
+        _check_data(t, plan, name, n)
+    _lib.check(_lib.load().chw_forward_haar(plan.handle, _ptr(x), _ptr(y), _ptr(z), _stream(stream)), "chw_forward_haar")
     return y
 
 

@@ -31,6 +31,7 @@ CHW_FLAG_NONE = 0
 CHW_FLAG_FORCE_SIMPLE = 1
 CHW_FLAG_FORCE_MULTIPASS = 2
 CHW_FLAG_ROWSTACK = 4
+CHW_FLAG_HAAR_WALSH = 8
 
 
 class chw_plan_info_t(ctypes.Structure):
@@ -58,6 +59,10 @@ _SIGNATURES = {
     "chw_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "chw_forward_ragged": (ctypes.c_int, [_P, _P, _P, _P]),
     "chw_forward_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "chw_haar": (ctypes.c_int, [_P, _P, _P, _P]),
+    "chw_haar_inverse": (ctypes.c_int, [_P, _P, _P, _P]),
+    "chw_from_haar": (ctypes.c_int, [_P, _P, _P, _P]),
+    "chw_forward_haar": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "chw_forward_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "chw_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(chw_plan_info_t)]),
     "chw_last_device_status": (ctypes.c_int, [_P]),

@@ -131,6 +131,21 @@ def _digest():
     return h.hexdigest()
 
 
+# Sources of the batched single-CTA and cluster kernels (the kernels the benchmark's roofline
+# record names); recorded next to committed DRAM-traffic figures so that a figure is used
+# only while the kernel it was measured on is unchanged.
+KERNEL_SOURCES = ("ptx.cuh", "engine.cuh", "fused.cuh", "launch.cuh")
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def build(force=False, verbose=False, jobs=None):
     """Compile every csrc/*.cu for sm_103a and link libchw.so; returns the library path."""
     digest = _digest()

@@ -24,6 +24,9 @@ LowpLaunchFn lookup_lowp(int m, bool f16, bool end);
 using RowstackLaunchFn = cudaError_t (*)(const CUtensorMap*, const FusedArgs&, uint32_t*, int64_t, int64_t,
                                          cudaStream_t);
 RowstackLaunchFn lookup_rowstack(int m, int var);
+int64_t haar_scratch_words(int m, int64_t batch);
+cudaError_t haar_forward(int var, int m, int64_t batch, const void* x, void* z, uint32_t* scratch, cudaStream_t st);
+cudaError_t haar_inverse(int var, int m, int64_t batch, const void* z, void* x, uint32_t* scratch, cudaStream_t st);
 }  // namespace chw
 
 namespace {
@@ -154,6 +157,13 @@ struct chw_plan_s {
   int8_t* h_diag = nullptr;
   // ragged
   chw::RaggedPlan* ragged = nullptr;
+  // Haar transforms: row approximations between passes (m > 13)
+  uint32_t* haar_ws = nullptr;
+  size_t haar_ws_bytes = 0;
+  // Haar-Walsh (CHW_FLAG_HAAR_WALSH): every Haar scale of every signal as one ragged task
+  // set (scales up to 2^20), and a one-signal plan per larger scale k
+  chw::RaggedPlan* hw = nullptr;
+  chw_plan_s* hw_big[CHW_MAX_M] = {};
 };
 
 namespace {
@@ -347,6 +357,61 @@ chw_status_t check_plan_args(int m, int64_t batch, chw_dtype_t dtype, chw_norm_t
   return CHW_OK;
 }
 
+// The Haar-Walsh task set of eq. (4): for every signal, z[0] (H = 1) and the Haar scale
+// k = 0..m-1 at [2^k, 2^{k+1}) (H_k).  Scales up to 2^20 run as one ragged task set over
+// these offsets; each larger scale k gets a one-signal plan of 2^k.
+chw_status_t build_haar_walsh(chw_plan_s* p) {
+  if (is_lowp(p->dtype)) return fail(CHW_ERR_UNSUPPORTED, "Haar-Walsh takes int32 or fp32");
+  if (p->m > 29) return fail(CHW_ERR_UNSUPPORTED, "Haar-Walsh takes m <= 29");
+  const int m = p->m;
+  const int kr = m - 1 < chw::kRaggedMaxM ? m - 1 : chw::kRaggedMaxM;
+  std::vector<uint8_t> ms;
+  std::vector<int64_t> off;
+  ms.reserve(static_cast<size_t>(p->batch) * (kr + 2));
+  off.reserve(ms.capacity());
+  for (int64_t s = 0; s < p->batch; ++s) {
+    const int64_t base = s << m;
+    ms.push_back(0);
+    off.push_back(base);
+    for (int k = 0; k <= kr; ++k) {
+      ms.push_back(static_cast<uint8_t>(k));
+      off.push_back(base + (int64_t{1} << k));
+    }
+  }
+  std::string why;
+  p->hw = chw::ragged_create_at(ms.data(), off.data(), static_cast<int64_t>(ms.size()), p->total,
+                                p->dtype == CHW_I32 ? chw::kVarI32 : fused_variant(p, true), p->d_status, &why);
+  if (p->hw == nullptr) return fail(CHW_ERR_CUDA, "Haar-Walsh task set: %s", why.c_str());
+  for (int k = chw::kRaggedMaxM + 1; k < m; ++k) {
+    chw_status_t r = chw_plan(&p->hw_big[k], k, 1, p->dtype, p->norm, 0);
+    if (r != CHW_OK) return r;
+  }
+  return CHW_OK;
+}
+
+// Read and clear a device status word (after a device synchronisation).
+chw_status_t take_status(int* d_status, int* out) {
+  CHW_CUDA(cudaMemcpy(out, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CHW_CUDA(cudaMemset(d_status, 0, sizeof(int)));
+  return CHW_OK;
+}
+
+// Two device ranges of `bytes` each overlap.
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
+chw_status_t check_haar_call(chw_plan_s* p, const void* in, const void* out, const char* in_name,
+                             const char* out_name) {
+  if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan is NULL");
+  if (p->ragged) return fail(CHW_ERR_INVALID_ARG, "Haar transforms take a batched plan, not a ragged one");
+  if (is_lowp(p->dtype)) return fail(CHW_ERR_UNSUPPORTED, "Haar transforms take int32 or fp32");
+  chw_status_t r = validate_data_ptr(in, in_name);
+  if (r != CHW_OK) return r;
+  return validate_data_ptr(out, out_name);
+}
+
 void destroy_host_pipeline(chw_plan_s* p) {
   for (int i = 0; i < 3; ++i) {
     if (p->h_stream[i]) cudaStreamDestroy(p->h_stream[i]);
@@ -468,6 +533,22 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
       return fail(CHW_ERR_OOM, "workspace of %zu bytes: %s", p->workspace_bytes, cudaGetErrorString(e));
     }
   }
+  if (!is_lowp(dtype)) {
+    p->haar_ws_bytes = static_cast<size_t>(chw::haar_scratch_words(m, batch)) * 4;
+    if (p->haar_ws_bytes > 0 && cudaMalloc(&p->haar_ws, p->haar_ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      chw_plan_destroy(p);
+      return fail(CHW_ERR_OOM, "Haar scratch of %zu bytes", p->haar_ws_bytes);
+    }
+  }
+  if ((flags & CHW_FLAG_HAAR_WALSH) != 0) {
+    r = build_haar_walsh(p);
+    if (r != CHW_OK) {
+      const std::string why = g_err;
+      chw_plan_destroy(p);
+      return fail(r, "%s", why.c_str());
+    }
+  }
   *out = p;
   return CHW_OK;
 }
@@ -478,6 +559,10 @@ chw_status_t chw_plan_destroy(chw_plan_t p) {
   if (p->workspace) cudaFree(p->workspace);
   if (p->d_status) cudaFree(p->d_status);
   if (p->ragged) chw::ragged_destroy(p->ragged);
+  if (p->haar_ws) cudaFree(p->haar_ws);
+  if (p->hw) chw::ragged_destroy(p->hw);
+  for (chw_plan_s* b : p->hw_big)
+    if (b) chw_plan_destroy(b);
   delete p;
   return CHW_OK;
 }
@@ -623,10 +708,70 @@ chw_status_t chw_last_device_status(chw_plan_t p) {
   if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan is NULL");
   CHW_CUDA(cudaDeviceSynchronize());
   int s = 0;
-  CHW_CUDA(cudaMemcpy(&s, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  CHW_CUDA(cudaMemset(p->d_status, 0, sizeof(int)));
+  chw_status_t r = take_status(p->d_status, &s);
+  if (r != CHW_OK) return r;
+  for (chw_plan_s* b : p->hw_big) {
+    if (b == nullptr) continue;
+    int sb = 0;
+    r = take_status(b->d_status, &sb);
+    if (r != CHW_OK) return r;
+    if (s == 0) s = sb;
+  }
   if (s != 0) return fail(static_cast<chw_status_t>(s), "device reported %s", chw_status_string(static_cast<chw_status_t>(s)));
   return CHW_OK;
+}
+
+chw_status_t chw_haar(chw_plan_t p, const void* x, void* z, void* stream) {
+  g_err.clear();
+  chw_status_t r = check_haar_call(p, x, z, "x", "z");
+  if (r != CHW_OK) return r;
+  if (overlaps(x, z, static_cast<size_t>(p->total) * 4)) return fail(CHW_ERR_INVALID_ARG, "x and z overlap");
+  CHW_CUDA(chw::haar_forward(fused_variant(p, true), p->m, p->batch, x, z, p->haar_ws,
+                             static_cast<cudaStream_t>(stream)));
+  return CHW_OK;
+}
+
+chw_status_t chw_haar_inverse(chw_plan_t p, const void* z, void* x, void* stream) {
+  g_err.clear();
+  chw_status_t r = check_haar_call(p, z, x, "z", "x");
+  if (r != CHW_OK) return r;
+  if (overlaps(x, z, static_cast<size_t>(p->total) * 4)) return fail(CHW_ERR_INVALID_ARG, "z and x overlap");
+  CHW_CUDA(chw::haar_inverse(fused_variant(p, true), p->m, p->batch, z, x, p->haar_ws,
+                             static_cast<cudaStream_t>(stream)));
+  return CHW_OK;
+}
+
+chw_status_t chw_from_haar(chw_plan_t p, const void* z, void* y, void* stream) {
+  g_err.clear();
+  chw_status_t r = check_haar_call(p, z, y, "z", "y");
+  if (r != CHW_OK) return r;
+  if (p->hw == nullptr) return fail(CHW_ERR_INVALID_ARG, "the plan was made without CHW_FLAG_HAAR_WALSH");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::string why;
+  if (chw::ragged_run(p->hw, z, y, st, &why) != 0) return fail(CHW_ERR_CUDA, "Haar-Walsh scales: %s", why.c_str());
+  for (int k = chw::kRaggedMaxM + 1; k < p->m; ++k) {
+    chw_plan_s* b = p->hw_big[k];
+    for (int64_t s = 0; s < p->batch; ++s) {
+      const int64_t o = (s << p->m) + (int64_t{1} << k);
+      r = run_transform(b, static_cast<const uint32_t*>(z) + o, static_cast<uint32_t*>(y) + o, 1, nullptr, nullptr,
+                        nullptr, nullptr, b->workspace, st);
+      if (r != CHW_OK) return r;
+    }
+  }
+  return CHW_OK;
+}
+
+chw_status_t chw_forward_haar(chw_plan_t p, const void* x, void* y, void* z, void* stream) {
+  g_err.clear();
+  chw_status_t r = check_haar_call(p, x, y, "x", "y");
+  if (r != CHW_OK) return r;
+  if (p->hw == nullptr) return fail(CHW_ERR_INVALID_ARG, "the plan was made without CHW_FLAG_HAAR_WALSH");
+  if (z == nullptr) return fail(CHW_ERR_INVALID_ARG, "z is NULL");
+  const size_t bytes = static_cast<size_t>(p->total) * 4;
+  if (overlaps(x, z, bytes) || overlaps(y, z, bytes)) return fail(CHW_ERR_INVALID_ARG, "z overlaps x or y");
+  r = chw_haar(p, x, z, stream);
+  if (r != CHW_OK) return r;
+  return chw_from_haar(p, z, y, stream);
 }
 
 chw_status_t chw_plan_ragged(chw_plan_t* out, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,

@@ -311,6 +311,14 @@ __device__ __forceinline__ void butterflies(uint32_t (&v)[64], const BF& bf) {
 // Butterfly (a, b) -> (a+b, a-b), values carried as 32-bit patterns.  The packed form
 // runs two butterflies with f32x2 instructions (per-lane IEEE round to nearest even, no
 // flush of subnormals: the same results as the scalar form).
+// fp32(2^{-m/2}) for 0 <= m <= 252: 2^{-floor(m/2)} times 1 or fp32(1/sqrt2).  Scaling the
+// correctly rounded constant by a power of two is exact in fp32's normal range, so the
+// result is 2^{-m/2} correctly rounded.
+__device__ __forceinline__ float end_scale_dev(int m) {
+  const float r = (m & 1) ? 0.70710678118654752440f : 1.0f;
+  return __fmul_rn(r, __uint_as_float(static_cast<uint32_t>(127 - m / 2) << 23));
+}
+
 struct BfF32Plain {
   static constexpr bool kPacked = true;
   __device__ __forceinline__ void operator()(uint32_t& a, uint32_t& b) const {

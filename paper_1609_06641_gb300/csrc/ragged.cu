@@ -21,6 +21,7 @@ struct RaggedPlan {
   std::vector<uint8_t> ms;
   std::vector<int64_t> off;  // count + 1 entries
   int64_t total = 0;
+  int64_t map_words = 0;  // extent of the input tensor map
   int variant = 0;
   int* d_status = nullptr;
   int ntasks = 0;
@@ -72,20 +73,27 @@ bool encode_rows(CUtensorMap* map, const void* ptr, int64_t words) {
 }  // namespace
 
 RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, std::string* why) {
-  auto* r = new RaggedPlan();
-  r->count = count;
-  r->ms.assign(ms, ms + count);
-  r->off.resize(count + 1);
-  r->variant = variant;
-  r->d_status = d_status;
+  std::vector<int64_t> off(count + 1);
   int64_t o = 0;
   for (int64_t i = 0; i < count; ++i) {
-    r->off[i] = o;
+    off[i] = o;
     o += int64_t{1} << ms[i];
     o = (o + 31) & ~int64_t{31};  // every signal starts on a 128-byte boundary
   }
-  r->off[count] = o;
-  r->total = o;
+  off[count] = o;
+  return ragged_create_at(ms, off.data(), count, o, variant, d_status, why);
+}
+
+RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t count, int64_t total, int variant,
+                             int* d_status, std::string* why) {
+  auto* r = new RaggedPlan();
+  r->count = count;
+  r->ms.assign(ms, ms + count);
+  r->off.assign(offsets, offsets + count);
+  r->off.push_back(total);
+  r->variant = variant;
+  r->d_status = d_status;
+  r->total = total;
 
   // ---- task table
   std::vector<RaggedTask> tasks;
@@ -160,6 +168,11 @@ RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_
   }
   r->ntasks = static_cast<int>(tasks.size());
   r->nctr = 1 + 2 * r->nbig;
+  // TILE/ROW/COL tasks read x through a tensor map of whole 32-word rows; without them the
+  // map is never used and one row stands in for arrays shorter than 32 words.
+  bool tma = false;
+  for (const RaggedTask& t : tasks) tma |= t.kind != kTaskSmall;
+  r->map_words = tma ? r->total : 32;
 
   cudaError_t e = cudaMalloc(&r->d_tasks, std::max<size_t>(1, tasks.size()) * sizeof(RaggedTask));
   if (e == cudaSuccess && !tasks.empty())
@@ -195,8 +208,9 @@ int ragged_run(RaggedPlan* r, const void* x, void* y, cudaStream_t st, std::stri
       r->exec = nullptr;
     }
     CUtensorMap tx, tr;
-    if (!encode_rows(&tx, x, r->total) || !encode_rows(&tr, r->d_ring ? static_cast<const void*>(r->d_ring) : x,
-                                                          r->d_ring ? kRingSlots * kRingSlotWords : r->total)) {
+    if (!encode_rows(&tx, x, r->map_words) ||
+        !encode_rows(&tr, r->d_ring ? static_cast<const void*>(r->d_ring) : x,
+                     r->d_ring ? kRingSlots * kRingSlotWords : r->map_words)) {
       *why = "cuTensorMapEncodeTiled failed";
       return 1;
     }

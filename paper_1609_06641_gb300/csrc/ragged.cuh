@@ -61,6 +61,10 @@ struct RaggedArgs {
 
 struct RaggedPlan;
 RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, std::string* why);
+// The same over caller-chosen offsets (elements of x and y; `total` = their length): signals
+// with m >= 14 must start on a 32-element boundary, shorter ones anywhere.
+RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t count, int64_t total, int variant,
+                             int* d_status, std::string* why);
 void ragged_destroy(RaggedPlan* r);
 int64_t ragged_total(const RaggedPlan* r);
 int ragged_passes(const RaggedPlan* r);

@@ -15,11 +15,6 @@ __device__ __forceinline__ void red_release_gpu_add(int32_t* p, int v) {
   asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ float end_scale_dev(int m) {  // fp32(2^{-m/2}), exact scaling
-  const float r = (m & 1) ? 0.70710678118654752440f : 1.0f;
-  return __fmul_rn(r, __uint_as_float(static_cast<uint32_t>(127 - m / 2) << 23));
-}
-
 // Signals with m <= 13, one after another: the cascade's butterflies level by level in
 // shared memory (level t pairs labels differing in bit t), then the dyadic reorder.
 template <class BF, bool SCALE>

@@ -1,0 +1,145 @@
+"""Haar transform (eq. (2)), its transpose, and the Haar-Walsh transform (eq. (4)) on the GPU.
+
+Every case compares the CUDA path, called through the C ABI, with the CPU oracle on the
+same seeded inputs, element by element: bit for bit wherever both sides take the same
+operations (all modes here), and the round trips within fp32 tolerance.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import assert_bitwise
+from paper_1609_06641_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ORACLE_DT = {"f32": np.float32, "i32": np.int32}
+
+
+@pytest.fixture(scope="module")
+def chw(cuda_device):
+    import paper_1609_06641_gb300 as chw
+    from paper_1609_06641_gb300 import build
+
+    build.build()
+    return chw
+
+
+def _inputs(m, batch, dtype, seed):
+    if dtype == "i32":
+        # |x| <= 2^(28-m) keeps every unnormalised coefficient (up to 2^m |x|) in int32
+        return W.uniform_int32(m, batch, seed, bound=1 << max(1, 28 - m))
+    return W.normal_f32(m, batch, seed)
+
+
+def _gpu(chw, fn, plan, a, out=None):
+    import torch
+
+    ad = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    od = torch.empty_like(ad) if out is None else out
+    fn(plan, ad, od)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(plan) == 0
+    return od.cpu().numpy()
+
+
+CASES = [(m, b) for m in range(0, 15) for b in (1, 3)] + [(5, 300), (12, 9), (13, 2), (14, 5), (16, 3), (20, 2), (22, 1)]
+MODES = [("f32", "per_level"), ("f32", "end"), ("f32", "none"), ("i32", "none")]
+
+
+@pytest.mark.parametrize("m,batch", CASES)
+@pytest.mark.parametrize("dtype,norm", MODES)
+def test_haar_forward_and_inverse_bitwise(chw, m, batch, dtype, norm):
+    x = _inputs(m, batch, dtype, 1000 + m)
+    p = chw.chw_plan(m, batch, dtype, norm)
+    z = _gpu(chw, chw.chw_haar, p, x)
+    assert_bitwise(z, O.haar_forward(x, m, ORACLE_DT[dtype], norm), f"Psi m={m} b={batch} {dtype} {norm}")
+    w = _gpu(chw, chw.chw_haar_inverse, p, z)
+    assert_bitwise(w, O.haar_inverse(z, m, ORACLE_DT[dtype], norm), f"Psi^T m={m} b={batch} {dtype} {norm}")
+    if norm != "none":
+        assert np.abs(w - x).max() <= 1e-5 * max(1.0, np.abs(x).max())
+
+
+@pytest.mark.parametrize("m", [26, 27])
+def test_haar_multi_pass_large(chw, m):
+    # two and three passes (13 + 13, 13 + 13 + 1 levels)
+    x = W.uniform_pm1_f32(m, 1, 3000 + m)
+    for norm in ("per_level", "end"):
+        p = chw.chw_plan(m, 1, "f32", norm)
+        z = _gpu(chw, chw.chw_haar, p, x)
+        assert_bitwise(z, O.haar_forward(x, m, np.float32, norm), f"Psi m={m} {norm}")
+        w = _gpu(chw, chw.chw_haar_inverse, p, z)
+        assert_bitwise(w, O.haar_inverse(z, m, np.float32, norm), f"Psi^T m={m} {norm}")
+
+
+HW_CASES = [(m, b) for m in range(0, 18) for b in (1, 2)] + [(10, 64), (13, 5), (16, 33), (20, 2), (21, 1), (22, 2)]
+
+
+@pytest.mark.parametrize("m,batch", HW_CASES)
+@pytest.mark.parametrize("dtype,norm", MODES)
+def test_haar_walsh_bitwise(chw, m, batch, dtype, norm):
+    z = _inputs(m, batch, dtype, 2000 + m)
+    p = chw.chw_plan(m, batch, dtype, norm, chw.CHW_FLAG_HAAR_WALSH)
+    y = _gpu(chw, chw.chw_from_haar, p, z)
+    assert_bitwise(y, O.haar_walsh(z, m, ORACLE_DT[dtype], norm), f"HW m={m} b={batch} {dtype} {norm}")
+
+
+@pytest.mark.parametrize("m,batch", [(3, 4), (12, 8), (16, 4), (18, 1)])
+def test_haar_walsh_in_place(chw, m, batch):
+    import torch
+
+    z = W.normal_f32(m, batch, 77)
+    p = chw.chw_plan(m, batch, "f32", "per_level", chw.CHW_FLAG_HAAR_WALSH)
+    zd = torch.from_numpy(z).cuda()
+    chw.chw_from_haar(p, zd, zd)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(p) == 0
+    assert_bitwise(zd.cpu().numpy(), O.haar_walsh(z, m, np.float32, "per_level"), "in place")
+
+
+@pytest.mark.parametrize("m,batch", [(1, 5), (9, 16), (14, 4), (16, 8), (19, 2)])
+@pytest.mark.parametrize("dtype,norm", [("f32", "per_level"), ("i32", "none"), ("f32", "end")])
+def test_forward_with_haar_side_output(chw, m, batch, dtype, norm):
+    import torch
+
+    x = _inputs(m, batch, dtype, 4000 + m)
+    p = chw.chw_plan(m, batch, dtype, norm, chw.CHW_FLAG_HAAR_WALSH)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    zd = torch.empty_like(xd)
+    chw.chw_forward_haar(p, xd, yd, zd)
+    y_ref = torch.empty_like(xd)
+    chw.chw_forward(p, xd, y_ref)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(p) == 0
+    dt = ORACLE_DT[dtype]
+    z_ref = O.haar_forward(x, m, dt, norm)
+    assert_bitwise(zd.cpu().numpy(), z_ref, "side output")
+    assert_bitwise(yd.cpu().numpy(), O.haar_walsh(z_ref, m, dt, norm), "stages 1..m-1")
+    if norm != "end":
+        # PER_LEVEL / NONE: the two halves of the cascade give chw_forward's bits
+        assert_bitwise(yd.cpu().numpy(), y_ref.cpu().numpy(), "same as chw_forward")
+        assert_bitwise(yd.cpu().numpy(), O.chw_cascade(x, m, dt, norm), "cascade")
+    else:
+        ref = O.wht_fast_dyadic(x.astype(np.float64), m)
+        assert O.rel_err_per_signal(yd.cpu().numpy(), ref).max() < 1e-6
+
+
+def test_haar_argument_errors(chw):
+    import torch
+
+    p = chw.chw_plan(10, 2, "f32", "end")
+    x = torch.zeros(2, 1024, device="cuda")
+    with pytest.raises(chw.ChwError, match="overlap"):
+        chw.chw_haar(p, x, x)
+    with pytest.raises(chw.ChwError, match="overlap"):
+        chw.chw_haar_inverse(p, x, x)
+    with pytest.raises(chw.ChwError, match="CHW_FLAG_HAAR_WALSH"):
+        chw.chw_from_haar(p, x, torch.empty_like(x))
+    q = chw.chw_plan(10, 2, "bf16", "end")
+    xb = torch.zeros(2, 1024, device="cuda", dtype=torch.bfloat16)
+    with pytest.raises(chw.ChwError, match="int32 or fp32"):
+        chw.chw_haar(q, xb, torch.empty_like(xb))
+    with pytest.raises(chw.ChwError):
+        chw.chw_plan(10, 2, "bf16", "end", chw.CHW_FLAG_HAAR_WALSH)
