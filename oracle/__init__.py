@@ -21,6 +21,7 @@ Walsh-Hadamard Transform", arXiv 1609.06641):
   cascade of inverse Haar transforms.
 * ``wavelets``     -- the Haar transform Psi_m of eq. (2), its transpose, and the
   Haar-Walsh transform H_m Psi_m^T of eq. (4) (stages 1..m-1 of Theorem 1).
+* ``orderings``    -- natural (Sylvester) and sequency (Walsh) orderings of the outputs.
 * ``lowp``         -- the bf16/fp16 storage form: per-signal power-of-two
   exponents decided in fp32, the same precision the kernels decide them in.
 * ``errors``       -- FP64 normwise relative error per signal.
@@ -51,6 +52,7 @@ from .transforms import (
     inv_sqrt2,
 )
 from .wavelets import haar_forward, haar_inverse, haar_levels, haar_walsh
+from .orderings import hadamard_natural, order_permutation, sign_changes, walsh_sequency_matrix, wht_ordered
 from .lowp import codes_to_f32, dequantise, lowp_forward_reference, round_to_bf16, round_to_f16
 from .errors import rel_err_per_signal
 
@@ -72,6 +74,11 @@ __all__ = [
     "OpCounter",
     "end_scale_f32",
     "inv_sqrt2",
+    "hadamard_natural",
+    "order_permutation",
+    "sign_changes",
+    "walsh_sequency_matrix",
+    "wht_ordered",
     "haar_forward",
     "haar_inverse",
     "haar_levels",
