@@ -354,6 +354,16 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     ms = time_device(lambda: chw.chw_forward_haar(ph, xh, yh, zh), k, warmup, 1, st)
     rec("m16_b4096_f32_forward_with_haar_output", 3 * nb, ms, 3)
     del xh, zh, yh, ph
+    # natural and sequency output orders on the headline shape and at m = 12
+    for order in ("natural", "sequency"):
+        for m, b in ((M, BATCH), (12, 65536)):
+            xo = torch.randn(b, 1 << m, device=dev, generator=g)
+            yo = torch.empty_like(xo)
+            po = chw.chw_plan(m, b, "f32", "end", order=order)
+            info = chw.chw_plan_get_info(po)
+            ms = time_device(lambda: chw.chw_forward(po, xo, yo), k, warmup, 1, st)
+            rec(f"m{m}_b{b}_f32_{order}", 2 * xo.numel() * 4, ms, info.kernels_per_call, tier=int(info.tier))
+            del xo, yo, po
     # ragged: 10,000 signals with m uniform on 6..20 (seed 5), one graph launch
     from paper_1609_06641_gb300 import workloads as W
 

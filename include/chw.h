@@ -74,6 +74,8 @@ typedef enum chw_norm_e {
 #define CHW_FLAG_ROWSTACK 4u        /* m = 15..17: one CTA per signal with its rows through */
                                     /* L2 instead of a thread-block cluster (DSMEM)        */
 #define CHW_FLAG_HAAR_WALSH 8u      /* also prepare chw_from_haar / chw_forward_haar       */
+#define CHW_FLAG_ORDER_NATURAL 16u  /* store outputs in natural (Sylvester) order          */
+#define CHW_FLAG_ORDER_SEQUENCY 32u /* store outputs in sequency (Walsh) order             */
 
 typedef struct chw_plan_s* chw_plan_t;
 
@@ -91,6 +93,7 @@ typedef struct chw_plan_info_s {
   int kernels_per_call;      /* kernel launches per forward/adjoint call               */
   int64_t workspace_bytes;   /* device scratch owned by the plan                       */
   int64_t total_elements;    /* elements per call (sum over the batch)                 */
+  int order;                 /* output order: 0 dyadic, 1 natural, 2 sequency          */
 } chw_plan_info_t;
 
 /*
@@ -101,6 +104,14 @@ typedef struct chw_plan_info_s {
  *          CHW_F16 take CHW_NORM_END or CHW_NORM_PER_LEVEL (the stored exponent carries
  *          the scale) and need m <= 13.
  *   flags  CHW_FLAG_* bits.
+ * Output order.  By default outputs are in dyadic order, y = H_m x with H_m of eq. (1).
+ * CHW_FLAG_ORDER_NATURAL stores the same values in natural (Sylvester-Hadamard) order,
+ * y_nat[k] = y[bitrev_m(k)], and CHW_FLAG_ORDER_SEQUENCY in sequency (Walsh) order,
+ * y_seq[k] = y[k ^ (k >> 1)] (row k has k sign changes).  The butterflies, and so every
+ * value, are those of the dyadic transform; only the store changes.  Both ordered
+ * matrices are symmetric, so chw_adjoint of an ordered plan is the same ordered transform
+ * (D then applied to its input).  Natural order takes m <= 23 (m >= 15 runs as two HBM
+ * passes); ordered plans cannot be combined with CHW_FLAG_ROWSTACK or ragged plans.
  * Allocates the plan (host) and its device workspace on the current device.  Returns
  * CHW_ERR_INVALID_ARG / CHW_ERR_UNSUPPORTED / CHW_ERR_OOM / CHW_ERR_CUDA on failure, in
  * which case *plan is set to NULL.

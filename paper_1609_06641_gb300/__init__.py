@@ -20,6 +20,8 @@ from ._lib import (
     CHW_F16,
     CHW_F32,
     CHW_FLAG_HAAR_WALSH,
+    CHW_FLAG_ORDER_NATURAL,
+    CHW_FLAG_ORDER_SEQUENCY,
     CHW_FLAG_ROWSTACK,
     CHW_FLAG_FORCE_MULTIPASS,
     CHW_FLAG_FORCE_SIMPLE,
@@ -34,6 +36,7 @@ from ._lib import (
 
 DTYPES = {"i32": CHW_I32, "f32": CHW_F32, "bf16": CHW_BF16, "f16": CHW_F16}
 NORMS = {"none": CHW_NORM_NONE, "per_level": CHW_NORM_PER_LEVEL, "end": CHW_NORM_END}
+ORDERS = {"dyadic": 0, "natural": CHW_FLAG_ORDER_NATURAL, "sequency": CHW_FLAG_ORDER_SEQUENCY}
 TIERS = {0: "simple", 1: "fused", 2: "cluster", 3: "two-pass", 4: "ragged", 5: "fused-16bit", 6: "row-stack"}
 
 
@@ -104,13 +107,17 @@ def _check_data(t, plan, name, numel):
         raise ValueError(f"{name} has {t.numel()} elements, the plan needs {numel}")
 
 
-def chw_plan(m, batch, dtype="f32", norm="end", flags=CHW_FLAG_NONE):
-    """Plan y = H_m x for ``batch`` signals of 2^m elements (see chw_plan in chw.h)."""
+def chw_plan(m, batch, dtype="f32", norm="end", flags=CHW_FLAG_NONE, order="dyadic"):
+    """Plan y = H_m x for ``batch`` signals of 2^m elements (see chw_plan in chw.h).
+
+    ``order`` ("dyadic", "natural" or "sequency") adds the matching CHW_FLAG_ORDER_* flag.
+    """
     lib = _lib.load()
     h = ctypes.c_void_p()
     d = _code(dtype, DTYPES, "dtype")
     nm = _code(norm, NORMS, "norm")
-    _lib.check(lib.chw_plan(ctypes.byref(h), int(m), int(batch), d, nm, int(flags)), "chw_plan")
+    flags = int(flags) | _code(order, ORDERS, "order")
+    _lib.check(lib.chw_plan(ctypes.byref(h), int(m), int(batch), d, nm, flags), "chw_plan")
     return Plan(h, int(m), int(batch), d, nm)
 
 

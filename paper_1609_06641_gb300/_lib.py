@@ -32,6 +32,8 @@ CHW_FLAG_FORCE_SIMPLE = 1
 CHW_FLAG_FORCE_MULTIPASS = 2
 CHW_FLAG_ROWSTACK = 4
 CHW_FLAG_HAAR_WALSH = 8
+CHW_FLAG_ORDER_NATURAL = 16
+CHW_FLAG_ORDER_SEQUENCY = 32
 
 
 class chw_plan_info_t(ctypes.Structure):
@@ -47,6 +49,7 @@ class chw_plan_info_t(ctypes.Structure):
         ("kernels_per_call", ctypes.c_int),
         ("workspace_bytes", ctypes.c_int64),
         ("total_elements", ctypes.c_int64),
+        ("order", ctypes.c_int),
     ]
 
 

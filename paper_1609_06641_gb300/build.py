@@ -59,6 +59,15 @@ SHAPES = (
     + [(0, m, 13, m - 13, 0, ALL) for m in (14, 15, 16)]
     + [(0, b, 13, b - 13, 1, NO_END) for b in (14, 15, 16)]
     + [(5, a, 13, a - 8, 0, ALL) for a in (9, 10, 11)]
+    # natural order (mode 2: final output, mode 4: first pass of the natural two-pass split)
+    + [(0, m, 13, 0, 2, ALL) for m in range(2, 14)]
+    + [(0, 14, 14, 0, 2, ALL)]
+    + [(0, b, 13 if b <= 13 else 14, 0, 4, NO_END) for b in range(5, 15)]
+    + [(5, a, 13 if a <= 8 else 14, 0, 2, ALL) for a in (6, 7, 8, 9)]
+    # sequency order (mode 3)
+    + [(0, m, 13, 0, 3, ALL) for m in range(2, 14)]
+    + [(0, 14, 14, 0, 3, ALL), (0, 15, 14, 1, 3, ALL), (0, 16, 14, 2, 3, ALL), (0, 17, 14, 3, 3, ALL)]
+    + [(5, a, 13 if a <= 8 else 14, max(0, a - 9), 3, ALL) for a in range(6, 13)]
 )
 BF = {
     "kVarPerLevel": ("::chw::BfF32PerLevel", "false"),

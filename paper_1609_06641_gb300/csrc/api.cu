@@ -144,6 +144,7 @@ struct chw_plan_s {
   int passes = 1;
   int row_bits = 0;  // two-pass: b (pass 1 rows); a = m - b
   int64_t rowstack_slots = 0;  // row-stack tier: scratch slots of 2^m words (one per CTA)
+  int order = 0;               // 0 dyadic, 1 natural, 2 sequency
   int64_t total = 0;
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
@@ -177,6 +178,13 @@ int fused_variant(const chw_plan_s* p, bool last_pass) {
   }
 }
 
+// Output mode of a final pass (fused.cuh): 0 dyadic, 2 natural, 3 sequency.  For m <= 1 the
+// three orders coincide.
+int final_outmode(const chw_plan_s* p) {
+  if (p->m <= 1) return 0;
+  return p->order == 1 ? 2 : (p->order == 2 ? 3 : 0);
+}
+
 chw_status_t validate_data_ptr(const void* p, const char* name) {
   if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "%s is NULL", name);
   if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return fail(CHW_ERR_ALIGNMENT, "%s is not 16-byte aligned", name);
@@ -201,16 +209,18 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
   a.diag_mask = diag_mask;
   a.status = p->d_status;
   a.colblock_a = colblock_a;
+  a.order_m = M;
+  a.nat_b = 0;
   const int64_t unit = int64_t{1} << (s.tb + s.cb);
   const int64_t units = s.cb > 0 ? total / unit : (total + unit - 1) / unit;
   CHW_CUDA(fn(&map, a, units, st));
   return CHW_OK;
 }
 
-chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, const void* in, void* out, int64_t total,
+chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, int om, const void* in, void* out, int64_t total,
                              const int8_t* diag_out, int64_t diag_mask, float scale, cudaStream_t st) {
-  const Shape s = col_shape(A);
-  chw::FusedLaunchFn fn = chw::lookup_fused(5, A, s.tb, s.cb, var, 0);
+  const Shape s = om == 2 ? Shape{A <= 8 ? 13 : 14, 0} : col_shape(A);
+  chw::FusedLaunchFn fn = chw::lookup_fused(5, A, s.tb, s.cb, var, om);
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no column kernel for A=%d", A);
   CUtensorMap map;
   chw_status_t r = make_rows_map(&map, in, total, s.tb);
@@ -224,6 +234,8 @@ chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, const void* in, void
   a.diag_mask = diag_mask;
   a.status = p->d_status;
   a.colblock_a = 0;
+  a.order_m = p->m;
+  a.nat_b = p->m - A;
   const int64_t unit = int64_t{1} << (s.tb + s.cb);
   const int64_t units = s.cb > 0 ? total / unit : (total + unit - 1) / unit;
   CHW_CUDA(fn(&map, a, units, st));
@@ -299,6 +311,7 @@ chw_status_t launch_simple(chw_plan_s* p, const void* x, void* y, int64_t batch,
   a.exp_out = exp_out;
   a.diag_in = diag_in;
   a.diag_out = diag_out;
+  a.order = p->order;
   const int64_t n = int64_t{1} << p->m;
   const int threads = n >= 512 ? 256 : (n >= 64 ? static_cast<int>(n / 2) : 32);
   const size_t smem = static_cast<size_t>(n) * 4;
@@ -330,14 +343,15 @@ chw_status_t run_transform(chw_plan_s* p, const void* x, void* y, int64_t batch,
       return launch_rowstack(p, x, y, batch, diag_in, diag_out, ws, p->rowstack_slots, st);
     case kTierFused:
     case kTierCluster:
-      return launch_row_pass(p, m, 0, fused_variant(p, true), x, y, total, diag_in, diag_out, dmask, 0,
-                             end_scale_f32(m), st);
+      return launch_row_pass(p, m, final_outmode(p), fused_variant(p, true), x, y, total, diag_in, diag_out, dmask,
+                             0, end_scale_f32(m), st);
     case kTierTwoPass: {
       const int b = p->row_bits, a = m - b;
-      chw_status_t r = launch_row_pass(p, b, 1, fused_variant(p, false), x, ws, total, diag_in, nullptr, dmask, a,
-                                       1.0f, st);
+      const int om2 = final_outmode(p);
+      chw_status_t r = launch_row_pass(p, b, om2 == 2 ? 4 : 1, fused_variant(p, false), x, ws, total, diag_in,
+                                       nullptr, dmask, a, 1.0f, st);
       if (r != CHW_OK) return r;
-      return launch_col_pass(p, a, fused_variant(p, true), ws, y, total, diag_out, dmask, end_scale_f32(m), st);
+      return launch_col_pass(p, a, fused_variant(p, true), om2, ws, y, total, diag_out, dmask, end_scale_f32(m), st);
     }
     default:
       return fail(CHW_ERR_INVALID_ARG, "plan is not a batched plan");
@@ -463,8 +477,33 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
   p->flags = flags;
   p->total = batch * (int64_t{1} << m);
   p->row_bits = m;
+  const bool nat = (flags & CHW_FLAG_ORDER_NATURAL) != 0, seq = (flags & CHW_FLAG_ORDER_SEQUENCY) != 0;
+  if (nat && seq) {
+    delete p;
+    return fail(CHW_ERR_INVALID_ARG, "CHW_FLAG_ORDER_NATURAL and CHW_FLAG_ORDER_SEQUENCY exclude each other");
+  }
+  p->order = nat ? 1 : (seq ? 2 : 0);
+  if (p->order != 0 && (flags & CHW_FLAG_ROWSTACK) != 0) {
+    delete p;
+    return fail(CHW_ERR_UNSUPPORTED, "ordered outputs are not available with CHW_FLAG_ROWSTACK");
+  }
 
-  if (is_lowp(dtype)) {
+  if (p->order != 0 && is_lowp(dtype)) {
+    if (m > 13) {
+      delete p;
+      return fail(CHW_ERR_UNSUPPORTED, "bf16/fp16 storage needs m <= 13 (one CTA per signal)");
+    }
+    p->tier = kTierSimple;  // the simple kernel stores any order
+  } else if (nat && m >= 15 && (flags & CHW_FLAG_FORCE_SIMPLE) == 0) {
+    // natural order: single-CTA rows, then columns written as stride-2^b runs
+    if (m > 23) {
+      delete p;
+      return fail(CHW_ERR_UNSUPPORTED, "natural order takes m <= 23");
+    }
+    p->tier = kTierTwoPass;
+    p->passes = 2;
+    p->row_bits = m - ((m - 14) > 6 ? (m - 14) : 6);
+  } else if (is_lowp(dtype)) {
     if (m > 13) {
       delete p;
       return fail(CHW_ERR_UNSUPPORTED, "bf16/fp16 storage needs m <= 13 (one CTA per signal)");
@@ -583,6 +622,7 @@ chw_status_t chw_plan_get_info(chw_plan_t p, chw_plan_info_t* info) {
   if (p->tier == kTierTwoPass) info->cluster = 1 << row_shape(p->row_bits).cb;
   info->workspace_bytes = static_cast<int64_t>(p->workspace_bytes);
   info->total_elements = p->total;
+  info->order = p->order;
   if (p->ragged) {
     info->kernels_per_call = 1;
     info->workspace_bytes = static_cast<int64_t>(chw::ragged_workspace_bytes(p->ragged));

@@ -14,6 +14,17 @@
 //            2^M x 32 block (32 columns of a row-transformed signal, stored contiguously
 //            by the first pass); the transform runs over the 2^M rows of each column and
 //            column c's results form the contiguous output row c (Y = H_b X^T H_a).
+//
+// Output modes (OUTMODE): where each result is stored.  The butterflies never change.
+//   0  dyadic order (the paper's H_m): label j is output bitrev(j);
+//   1  column-blocked scratch for the first pass of the two-pass split (dyadic rows);
+//   2  natural (Sylvester) order: label j is output j.  Row tiles stage in natural order;
+//      column tiles write each of their 32 columns as a stride-2^b run (the first pass ran
+//      in mode 4), where b = FusedArgs::nat_b is the first pass's bit count;
+//   3  sequency (Walsh) order: dyadic output p is sequency output gray^{-1}(p).  Tiles
+//      stage in dyadic order; the copy-out sends each aligned 4-element chunk to
+//      gray^{-1} of its position, which keeps the chunk together (reordered inside);
+//   4  column-blocked scratch with natural row order (first pass of a natural two-pass).
 #pragma once
 
 #include "engine.cuh"
@@ -32,7 +43,9 @@ struct FusedArgs {
   const int8_t* diag_out;    // +-1 applied to outputs (forward's D), or nullptr
   int64_t diag_mask;         // index within a signal = element index & diag_mask
   int* status;               // device status word (first error wins)
-  int colblock_a;            // OUTMODE 1: rows per signal = 2^colblock_a
+  int colblock_a;            // OUTMODE 1, 4: rows per signal = 2^colblock_a
+  int order_m;               // OUTMODE 3: bits of a signal (sequency order is per signal)
+  int nat_b;                 // OUTMODE 2, column tiles: the first pass's bits (row stride 2^b)
 };
 
 // ------------------------------------------------------------------ phase plans
@@ -47,8 +60,11 @@ struct FusedPlan {
   int rank_shift[4];  // o bit of each CTA-rank label bit (cluster output placement)
 };
 
-constexpr Lin make_omap(int TLO, int M) {
+constexpr bool natural_mode(int OM) { return OM == 2 || OM == 4; }
+
+constexpr Lin make_omap(int TLO, int M, int OM) {
   Lin l = lin_identity();
+  if (natural_mode(OM)) return l;  // natural order: label j is output j
   if (TLO == 0) {
     for (int b = 0; b < M; ++b) l.img[b] = 1u << (M - 1 - b);
   } else {
@@ -260,7 +276,7 @@ constexpr int pick_stage_key(const Phase& fw, const Lin& omap, int TB) {
   return 5;
 }
 
-constexpr FusedPlan make_plan(int TLO, int M, int TB, int CB) {
+constexpr FusedPlan make_plan(int TLO, int M, int TB, int CB, int OM) {
   FusedPlan f{};
   const int top = TLO + M;  // one past the last transform bit
   f.has_p1 = TLO == 0;
@@ -270,7 +286,7 @@ constexpr FusedPlan make_plan(int TLO, int M, int TB, int CB) {
   f.p1 = make_p1(TB);
   f.p2 = make_p2(TB, TLO, M);
   f.p3 = make_p3(TB, CB, TLO, M);
-  f.omap = make_omap(TLO, M);
+  f.omap = make_omap(TLO, M, OM);
   f.lin_s = lin_tma128();
   f.lin_b = make_lin_b(f.p2, f.p3);
   f.lin_r = CB > 0 ? make_lin_r(f.p2, f.p3, TB + CB) : lin_identity();
@@ -291,13 +307,16 @@ constexpr FusedPlan make_plan(int TLO, int M, int TB, int CB) {
   return f;
 }
 
-template <int TLO, int M, int TB, int CB>
+template <int TLO, int M, int TB, int CB, int OM = 0>
 struct FusedCfg {
-  static constexpr FusedPlan plan = make_plan(TLO, M, TB, CB);
+  static constexpr FusedPlan plan = make_plan(TLO, M, TB, CB, OM);
   static constexpr int NB = TB + CB;
   static constexpr uint32_t LMASK = (1u << TB) - 1u;
   static_assert(TB >= 11 && TB <= 15, "tile must hold 64 values x 32 lanes x >=1 warp");
   static_assert(TLO == 0 || TLO == 5, "transform starts at label bit 0 (rows) or 5 (columns)");
+  static_assert(OM >= 0 && OM <= 4, "output modes 0..4");
+  static_assert(!natural_mode(OM) || CB == 0, "natural order is staged by single-CTA tiles");
+  static_assert(OM != 4 || TLO == 0, "mode 4 is a first (row) pass");
   static_assert(CB == 0 || TLO + M == NB, "a cluster tile holds exactly one transform");
   static_assert(TLO + M <= NB && M >= 0, "transform must fit the tile");
   static_assert(TLO + M <= 17, "at most three register phases");
@@ -346,7 +365,7 @@ __device__ __forceinline__ void tile_issue(const CUtensorMap* tin, int in_row0, 
 // 16-byte stores; `out_base` is the element index of the (cluster) tile's first output.
 template <int TLO, int M, int TB, int CB, class BF, int OUTMODE>
 __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, uint32_t rank, const FusedArgs& args) {
-  using Cfg = FusedCfg<TLO, M, TB, CB>;
+  using Cfg = FusedCfg<TLO, M, TB, CB, OUTMODE>;
   constexpr FusedPlan F = Cfg::plan;
   constexpr int NT = 1 << (TB - 6);
   if constexpr (CB > 0) {
@@ -363,11 +382,44 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
     const uint32_t o = static_cast<uint32_t>(c) << 2;
     const uint32_t pos = o ^ (((o >> S) & 7u) << 2);
     uint4 q = *reinterpret_cast<const uint4*>(buf + pos);
-    const int64_t og = out_base + o;
+    const int64_t og = out_base + o;  // position in the staged (dyadic or natural) order
     if (og >= args.out_total) continue;
+    int64_t addr;
+    if constexpr (OUTMODE == 0 || (OUTMODE == 2 && TLO == 0)) {
+      addr = og;
+    } else if constexpr (OUTMODE == 1 || OUTMODE == 4) {
+      // Column-blocked scratch for the two-pass split: element k of row R of a signal with
+      // 2^a rows goes to signal*2^(a+M) + (k/32)*2^(a+5) + (R mod 2^a)*32 + k mod 32.
+      const int a = args.colblock_a;
+      const int64_t R = og >> M;
+      const int64_t k = og & ((int64_t{1} << M) - 1);
+      const int64_t sig = R >> a, r = R & ((int64_t{1} << a) - 1);
+      addr = (sig << (a + M)) + ((k >> 5) << (a + 5)) + (r << 5) + (k & 31);
+    } else if constexpr (OUTMODE == 2) {
+      // natural column tile: staged element c + 32 R + 2^(5+M) blk is row label R of column
+      // 32 cb + c of signal sig, where blk = sig 2^(b-5) + cb numbers the column blocks
+      const int b = args.nat_b;
+      const int64_t blk = og >> (5 + M);
+      const int64_t sig = blk >> (b - 5), cb = blk & ((int64_t{1} << (b - 5)) - 1);
+      const int64_t R = (og >> 5) & ((int64_t{1} << M) - 1);
+      addr = (sig << (M + b)) + (R << b) + (cb << 5) + (og & 31);
+    } else {
+      // sequency: dyadic position p = 4h + e (within the signal) goes to gray^{-1}(p)
+      // = 4 gray^{-1}(h) + (e-th entry of {0,1,3,2}, or of {3,2,0,1} when h has odd parity)
+      const int64_t p0 = og & ((int64_t{1} << args.order_m) - 1);
+      const uint32_t h = static_cast<uint32_t>(p0 >> 2);
+      uint32_t g = h;
+      g ^= g >> 1;
+      g ^= g >> 2;
+      g ^= g >> 4;
+      g ^= g >> 8;
+      g ^= g >> 16;
+      addr = (og - p0) + (static_cast<int64_t>(g) << 2);
+      q = (__popc(h) & 1) ? make_uint4(q.z, q.w, q.y, q.x) : make_uint4(q.x, q.y, q.w, q.z);
+    }
     if (args.diag_out != nullptr) {
       const int8_t* d = args.diag_out;
-      const int64_t di = og & args.diag_mask;
+      const int64_t di = addr & args.diag_mask;  // D acts on the stored (final) positions
       if constexpr (std::is_same_v<BF, BfI32>) {
         if (d[di] < 0) q.x = 0u - q.x;
         if (d[di + 1] < 0) q.y = 0u - q.y;
@@ -379,18 +431,6 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
         if (d[di + 2] < 0) q.z ^= 0x80000000u;
         if (d[di + 3] < 0) q.w ^= 0x80000000u;
       }
-    }
-    int64_t addr;
-    if constexpr (OUTMODE == 0) {
-      addr = og;
-    } else {
-      // Column-blocked scratch for the two-pass split: element k of row R of a signal with
-      // 2^a rows goes to signal*2^(a+M) + (k/32)*2^(a+5) + (R mod 2^a)*32 + k mod 32.
-      const int a = args.colblock_a;
-      const int64_t R = og >> M;
-      const int64_t k = og & ((int64_t{1} << M) - 1);
-      const int64_t sig = R >> a, r = R & ((int64_t{1} << a) - 1);
-      addr = (sig << (a + M)) + ((k >> 5) << (a + 5)) + (r << 5) + (k & 31);
     }
     st_global_v4(out + addr, q.x, q.y, q.z, q.w);
   }
@@ -451,7 +491,7 @@ __device__ __forceinline__ void push_to_finishers(const uint32_t (&v)[64], uint3
 template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
 __device__ __forceinline__ void phase_3_out(int64_t out_base, const FusedArgs& args, uint32_t* buf, uint32_t rank,
                                             const BF& bf) {
-  constexpr FusedPlan F = FusedCfg<TLO, M, TB, CB>::plan;
+  constexpr FusedPlan F = FusedCfg<TLO, M, TB, CB, OUTMODE>::plan;
   constexpr Phase P3 = F.p3, FW = F.fw;
   constexpr Lin LR = F.lin_r, LF = F.lin_final;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -476,7 +516,7 @@ template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
 __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base, const FusedArgs& args,
                                              uint32_t* buf, uint64_t* bar, uint32_t parity) {
   static_assert(CB == 0, "cluster tiles run in the pipelined cluster kernel");
-  using Cfg = FusedCfg<TLO, M, TB, CB>;
+  using Cfg = FusedCfg<TLO, M, TB, CB, OUTMODE>;
   constexpr FusedPlan F = Cfg::plan;
   constexpr uint32_t LMASK = Cfg::LMASK;
   constexpr Phase P1 = F.p1, P2 = F.p2, P3 = F.p3, FW = F.fw;

@@ -26,6 +26,7 @@ struct SimpleArgs {
   int32_t* exp_out;
   const int8_t* diag_in;
   const int8_t* diag_out;
+  int order;  // output order: 0 dyadic, 1 natural, 2 sequency
 };
 
 // floor(log2 v) for a finite v > 0, read from the fp32 encoding (exact, subnormals too).
@@ -129,9 +130,17 @@ __global__ void __launch_bounds__(256) simple_kernel(const SimpleArgs a) {
     }
   }
 
-  // store in dyadic order: output k holds label bitrev_m(k)
+  // store: the value of label j is the dyadic output bitrev_m(j), so dyadic output k holds
+  // label bitrev_m(k), natural output k label k, and sequency output k (= dyadic output
+  // gray(k)) label bitrev_m(k ^ (k >> 1))
+  const int rs = m == 0 ? 0 : 32 - m;  // __brev(v) >> rs reverses the low m bits (m >= 1)
   for (int64_t k = tid; k < n; k += blockDim.x) {
-    const int64_t lab = m == 0 ? 0 : static_cast<int64_t>(__brev(static_cast<uint32_t>(k)) >> (32 - m));
+    int64_t lab = 0;
+    if (m > 0) {
+      const uint32_t kk = static_cast<uint32_t>(k);
+      const uint32_t d = a.order == 1 ? __brev(kk) >> rs : (a.order == 2 ? kk ^ (kk >> 1) : kk);
+      lab = static_cast<int64_t>(__brev(d) >> rs);
+    }
     uint32_t v = s[lab];
     if (a.diag_out != nullptr && a.diag_out[k] < 0) v = kInt ? 0u - v : v ^ 0x80000000u;
     const int64_t g = sig * n + k;
