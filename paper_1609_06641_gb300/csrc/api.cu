@@ -65,6 +65,17 @@ int cluster_tile_bits() {
   return v;
 }
 
+// Column bits of the two-pass split for m = 18..29: a = max(6, m - 17) keeps the first
+// pass in one HBM round trip; CHW_TWO_PASS_A (6..12, with m - a <= 17) overrides it.
+int two_pass_col_bits(int m) {
+  static const int v = [] {
+    const char* e = std::getenv("CHW_TWO_PASS_A");
+    return e ? std::atoi(e) : 0;
+  }();
+  if (v >= 6 && v <= 12 && m - v <= 17 && m - v >= 5) return v;
+  return (m - 17) > 6 ? (m - 17) : 6;
+}
+
 // One-pass row kernel shape for a transform of M bits.
 Shape row_shape(int M) {
   if (M <= 13) return {13, 0};
@@ -530,7 +541,7 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
   } else if (m <= 29) {
     p->tier = kTierTwoPass;
     p->passes = 2;
-    const int a = (m - 17) > 6 ? (m - 17) : 6;
+    const int a = two_pass_col_bits(m);
     p->row_bits = m - a;
   } else {
     delete p;

@@ -695,8 +695,20 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
   auto par = [](int64_t u) { return static_cast<uint32_t>((u / kClusterBufs) & 1); };
   BF bf{};
   if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
-  auto timeout = [&]() {
-    if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+  // A wait that gives up records CHW_ERR_TIMEOUT and turns every later wait of this thread
+  // off, so a broken schedule costs one bounded wait per thread, not one per unit.
+  bool waiting = true;
+  auto wait_local = [&](uint64_t* b, uint32_t parity) {
+    if (waiting && !mbar_wait_bounded(b, parity, kWaitTries)) {
+      waiting = false;
+      if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+    }
+  };
+  auto wait_cluster = [&](uint64_t* b, uint32_t parity) {
+    if (waiting && !mbar_wait_cluster_bounded(b, parity, kWaitTries)) {
+      waiting = false;
+      if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+    }
   };
 
   if (tid == 0 && K > 0) tile_issue<TB>(&tin, row0(0), buf(0), tma);
@@ -706,19 +718,19 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
     if (k >= 1) {
       // ---- finish unit k-1: its pushes R_{k-1} sit in buffer (k-2) mod 3
       const int64_t u = k - 1;
-      if (!mbar_wait_cluster_bounded(fullb + u % kClusterBufs, par(u), kWaitTries)) timeout();
+      wait_cluster(fullb + u % kClusterBufs, par(u));
       phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>((first + u * stride) << (TB + CB), args, buf(u + 2), rank, bf);
       __syncthreads();  // buffer (k+1) mod 3 is free: the copy-out has read it
       if (tid == 0 && k + 1 < K) tile_issue<TB>(&tin, row0(k + 1), buf(k + 1), tma + (k + 1) % kClusterBufs);
     }
     if (k < K) {
       // ---- phases 1-2 of unit k, then push R_k
-      if (!mbar_wait_bounded(tma + k % kClusterBufs, par(k), kWaitTries)) timeout();
+      wait_local(tma + k % kClusterBufs, par(k));
       uint32_t v[64];
       phases_1_2<TLO, M, TB, CB, BF>(v, static_cast<int64_t>(row0(k)) * 32, args, buf(k), bf);
       __syncthreads();  // buffer k mod 3 is no longer read: it may receive R_{k+1}
       if (tid < NR) mbar_remote_arrive(freeb + (k + 1) % kClusterBufs, tid);
-      if (!mbar_wait_cluster_bounded(freeb + k % kClusterBufs, par(k), kWaitTries)) timeout();
+      wait_cluster(freeb + k % kClusterBufs, par(k));
       push_to_finishers<TLO, M, TB, CB>(v, buf(k + 2), rank);
       __syncthreads();  // every push of this CTA is issued
       if (tid < NR) {
