@@ -53,7 +53,7 @@ NO_END = ("kVarPerLevel", "kVarPlain", "kVarI32")
 SHAPES = (
     [(0, m, 13, 0, 0, ALL) for m in range(0, 14)]
     + [(0, 14, 14, 0, 0, ALL), (0, 15, 14, 1, 0, ALL), (0, 16, 14, 2, 0, ALL), (0, 17, 14, 3, 0, ALL)]
-    + [(0, b, 13 if b <= 13 else 14, max(0, b - 14), 1, NO_END) for b in (5, 8, 12, 13, 14, 15, 16, 17)]
+    + [(0, b, 13 if b <= 13 else 14, max(0, b - 14), 1, NO_END) for b in (5, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17)]
     + [(5, a, 13 if a <= 8 else 14, max(0, a - 9), 0, ALL) for a in range(6, 13)]
     # 2^13-word tiles in 2-, 4- and 8-CTA clusters (three CTAs per SM)
     + [(0, m, 13, m - 13, 0, ALL) for m in (14, 15, 16)]

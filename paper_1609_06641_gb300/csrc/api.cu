@@ -65,15 +65,19 @@ int cluster_tile_bits() {
   return v;
 }
 
-// Column bits of the two-pass split for m = 18..29: a = max(6, m - 17) keeps the first
-// pass in one HBM round trip; CHW_TWO_PASS_A (6..12, with m - a <= 17) overrides it.
+// Column bits a of the two-pass split y = H_b X^T H_a for m = 18..29 (b = m - a row bits).
+// Measured on GB300 (fp32, 1 GiB per call): single-CTA tiles in both passes are fastest,
+// with a = 9 (2^9 x 32 column blocks in one CTA); from m = 24 on, where b = m - 9 would
+// need cluster rows, a = 11 (4-CTA column clusters, single-CTA rows up to m = 25) wins,
+// and m = 29 takes a = 12.  CHW_TWO_PASS_A (6..12, m - a in 5..17) overrides it (tuning).
 int two_pass_col_bits(int m) {
   static const int v = [] {
     const char* e = std::getenv("CHW_TWO_PASS_A");
     return e ? std::atoi(e) : 0;
   }();
   if (v >= 6 && v <= 12 && m - v <= 17 && m - v >= 5) return v;
-  return (m - 17) > 6 ? (m - 17) : 6;
+  if (m <= 23) return 9;
+  return m <= 28 ? 11 : 12;
 }
 
 // One-pass row kernel shape for a transform of M bits.
@@ -513,7 +517,7 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     }
     p->tier = kTierTwoPass;
     p->passes = 2;
-    p->row_bits = m - ((m - 14) > 6 ? (m - 14) : 6);
+    p->row_bits = m - (m >= 18 ? 9 : 6);
   } else if (is_lowp(dtype)) {
     if (m > 13) {
       delete p;
