@@ -64,6 +64,9 @@ SHAPES = (
     + [(0, 14, 14, 0, 2, ALL)]
     + [(0, b, 13 if b <= 13 else 14, 0, 4, NO_END) for b in range(5, 15)]
     + [(5, a, 13 if a <= 8 else 14, 0, 2, ALL) for a in (6, 7, 8, 9)]
+    # the Haar-Walsh head (mode 6: per-scale transforms of a signal's first 2^m positions)
+    + [(0, m, 13, 0, 6, NO_END) for m in range(0, 14)]
+    + [(0, 14, 14, 0, 6, NO_END)]
     # sequency order (mode 3)
     + [(0, m, 13, 0, 3, ALL) for m in range(2, 14)]
     + [(0, 14, 14, 0, 3, ALL), (0, 15, 14, 1, 3, ALL), (0, 16, 14, 2, 3, ALL), (0, 17, 14, 3, 3, ALL)]

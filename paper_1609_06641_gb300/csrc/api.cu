@@ -178,7 +178,8 @@ struct chw_plan_s {
   size_t haar_ws_bytes = 0;
   // Haar-Walsh (CHW_FLAG_HAAR_WALSH): every Haar scale of every signal as one ragged task
   // set (scales up to 2^20), and a one-signal plan per larger scale k
-  chw::RaggedPlan* hw = nullptr;
+  chw::RaggedPlan* hw = nullptr;  // only for tiny totals that are not whole 32-word rows
+  bool hw_ready = false;
   chw_plan_s* hw_big[CHW_MAX_M] = {};
 };
 
@@ -386,13 +387,24 @@ chw_status_t check_plan_args(int m, int64_t batch, chw_dtype_t dtype, chw_norm_t
   return CHW_OK;
 }
 
-// The Haar-Walsh task set of eq. (4): for every signal, z[0] (H = 1) and the Haar scale
-// k = 0..m-1 at [2^k, 2^{k+1}) (H_k).  Scales up to 2^20 run as one ragged task set over
-// these offsets; each larger scale k gets a one-signal plan of 2^k.
+// The Haar-Walsh transform of eq. (4): for every signal, z[0] (H = 1) and the Haar scale
+// k = 0..m-1 at [2^k, 2^{k+1}) (H_k).  The scales below 2^14 together fill the signal's
+// first 2^min(m,14) positions and run in one single-CTA "head" launch (output mode 6);
+// scales k = 14..17 run as batched launches over strided units (one unit per signal,
+// 2^m apart, at offset 2^k); each scale k >= 18 gets a one-signal two-pass plan.  Totals
+// that are not whole 32-word rows (m < 5) take a ragged task set over the same offsets.
 chw_status_t build_haar_walsh(chw_plan_s* p) {
   if (is_lowp(p->dtype)) return fail(CHW_ERR_UNSUPPORTED, "Haar-Walsh takes int32 or fp32");
   if (p->m > 29) return fail(CHW_ERR_UNSUPPORTED, "Haar-Walsh takes m <= 29");
   const int m = p->m;
+  if (p->total % 32 == 0) {
+    for (int k = 18; k < m; ++k) {
+      chw_status_t r = chw_plan(&p->hw_big[k], k, 1, p->dtype, p->norm, 0);
+      if (r != CHW_OK) return r;
+    }
+    p->hw_ready = true;
+    return CHW_OK;
+  }
   const int kr = m - 1 < chw::kRaggedMaxM ? m - 1 : chw::kRaggedMaxM;
   std::vector<uint8_t> ms;
   std::vector<int64_t> off;
@@ -414,6 +426,64 @@ chw_status_t build_haar_walsh(chw_plan_s* p) {
   for (int k = chw::kRaggedMaxM + 1; k < m; ++k) {
     chw_status_t r = chw_plan(&p->hw_big[k], k, 1, p->dtype, p->norm, 0);
     if (r != CHW_OK) return r;
+  }
+  return CHW_OK;
+}
+
+// One launch of fused row tiles over `units` units of 2^(tb+cb) elements, unit u at
+// ubase + u * ustride (ustride 0: back to back), in and out both `total` words long.
+chw_status_t launch_units(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
+                          int64_t units, int64_t ustride, int64_t ubase, float scale, int head_end,
+                          cudaStream_t st) {
+  const Shape s = row_shape(M);
+  chw::FusedLaunchFn fn = chw::lookup_fused(0, M, s.tb, s.cb, var, om);
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no row kernel for M=%d tb=%d cb=%d out=%d", M, s.tb, s.cb, om);
+  CUtensorMap map;
+  chw_status_t r = make_rows_map(&map, in, total, s.tb);
+  if (r != CHW_OK) return r;
+  chw::FusedArgs a{};
+  a.out = out;
+  a.out_total = total;
+  a.end_scale = scale;
+  a.diag_mask = (int64_t{1} << p->m) - 1;
+  a.status = p->d_status;
+  a.order_m = M;
+  a.head_end = head_end;
+  a.unit_stride = ustride;
+  a.unit_base = ubase;
+  CHW_CUDA(fn(&map, a, units, st));
+  return CHW_OK;
+}
+
+// y = H_m Psi_m^T z (eq. (4)) with the launches described at build_haar_walsh.
+chw_status_t run_haar_walsh(chw_plan_s* p, const void* z, void* y, cudaStream_t st) {
+  const int m = p->m;
+  const int64_t total = p->total, n = int64_t{1} << m;
+  // the head's butterflies are unscaled for END (each scale is scaled once on output)
+  const int vh = p->dtype == CHW_I32 ? chw::kVarI32 : (p->norm == CHW_NORM_PER_LEVEL ? chw::kVarPerLevel : chw::kVarPlain);
+  const int head_end = p->dtype == CHW_F32 && p->norm == CHW_NORM_END;
+  chw_status_t r;
+  if (m <= 14) {
+    const Shape s = row_shape(m);
+    const int64_t tile = int64_t{1} << s.tb;
+    r = launch_units(p, m, 6, vh, z, y, total, (total + tile - 1) / tile, 0, 0, 1.0f, head_end, st);
+  } else {
+    r = launch_units(p, 14, 6, vh, z, y, total, p->batch, n, 0, 1.0f, head_end, st);
+  }
+  if (r != CHW_OK) return r;
+  for (int k = 14; k < m && k <= 17; ++k) {
+    r = launch_units(p, k, 0, fused_variant(p, true), z, y, total, p->batch, n, int64_t{1} << k, end_scale_f32(k), 0,
+                     st);
+    if (r != CHW_OK) return r;
+  }
+  for (int k = 18; k < m; ++k) {
+    chw_plan_s* b = p->hw_big[k];
+    for (int64_t s = 0; s < p->batch; ++s) {
+      const int64_t o = (s << m) + (int64_t{1} << k);
+      r = run_transform(b, static_cast<const uint32_t*>(z) + o, static_cast<uint32_t*>(y) + o, 1, nullptr, nullptr,
+                        nullptr, nullptr, b->workspace, st);
+      if (r != CHW_OK) return r;
+    }
   }
   return CHW_OK;
 }
@@ -800,8 +870,9 @@ chw_status_t chw_from_haar(chw_plan_t p, const void* z, void* y, void* stream) {
   g_err.clear();
   chw_status_t r = check_haar_call(p, z, y, "z", "y");
   if (r != CHW_OK) return r;
-  if (p->hw == nullptr) return fail(CHW_ERR_INVALID_ARG, "the plan was made without CHW_FLAG_HAAR_WALSH");
+  if (p->hw == nullptr && !p->hw_ready) return fail(CHW_ERR_INVALID_ARG, "the plan was made without CHW_FLAG_HAAR_WALSH");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p->hw_ready) return run_haar_walsh(p, z, y, st);
   std::string why;
   if (chw::ragged_run(p->hw, z, y, st, &why) != 0) return fail(CHW_ERR_CUDA, "Haar-Walsh scales: %s", why.c_str());
   for (int k = chw::kRaggedMaxM + 1; k < p->m; ++k) {
@@ -820,7 +891,7 @@ chw_status_t chw_forward_haar(chw_plan_t p, const void* x, void* y, void* z, voi
   g_err.clear();
   chw_status_t r = check_haar_call(p, x, y, "x", "y");
   if (r != CHW_OK) return r;
-  if (p->hw == nullptr) return fail(CHW_ERR_INVALID_ARG, "the plan was made without CHW_FLAG_HAAR_WALSH");
+  if (p->hw == nullptr && !p->hw_ready) return fail(CHW_ERR_INVALID_ARG, "the plan was made without CHW_FLAG_HAAR_WALSH");
   if (z == nullptr) return fail(CHW_ERR_INVALID_ARG, "z is NULL");
   const size_t bytes = static_cast<size_t>(p->total) * 4;
   if (overlaps(x, z, bytes) || overlaps(y, z, bytes)) return fail(CHW_ERR_INVALID_ARG, "z overlaps x or y");

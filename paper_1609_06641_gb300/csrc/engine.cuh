@@ -282,6 +282,32 @@ __device__ __forceinline__ void load_phase_cluster(uint32_t (&v)[64], const uint
   });
 }
 
+// The butterflies of the Haar-Walsh head (a 2^HM-element prefix, see fused.cuh OUTMODE 6):
+// the pair at bit b whose labels have no bit in [b+1, HM) set is stage 0's (the Haar
+// transform's) and is skipped.  `tl` = the thread's label bits; reg bits are compile time.
+template <Phase P, int LO, int HI, int HM, class BF>
+__device__ __forceinline__ void butterflies_head(uint32_t (&v)[64], const BF& bf, uint32_t tl) {
+  sfor<kMaxBits>([&](auto bb) {
+    constexpr int b = bb;
+    if constexpr (b >= LO && b < HI) {
+      constexpr int i = reg_index_of(P, b);
+      static_assert(i >= 0, "a butterfly bit must be a register bit of its phase");
+      constexpr uint32_t above = ((1u << HM) - 1u) & ~((2u << b) - 1u);
+      const bool live = (tl & above) != 0u;
+      sfor<64>([&](auto kk) {
+        constexpr int k = kk;
+        if constexpr (((k >> i) & 1) == 0) {
+          if constexpr ((reg_label(P, k) & above) != 0u) {
+            bf(v[k], v[k | (1 << i)]);
+          } else {
+            if (live) bf(v[k], v[k | (1 << i)]);
+          }
+        }
+      });
+    }
+  });
+}
+
 // Butterflies of phase P on the label bits in [LO, HI), lowest bit first.  When the
 // functor has a packed form (two butterflies in one f32x2 instruction pair) and register
 // bit 0 is not the butterfly bit, registers k and k|1 travel together.

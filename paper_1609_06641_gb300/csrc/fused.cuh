@@ -24,7 +24,13 @@
 //   3  sequency (Walsh) order: dyadic output p is sequency output gray^{-1}(p).  Tiles
 //      stage in dyadic order; the copy-out sends each aligned 4-element chunk to
 //      gray^{-1} of its position, which keeps the chunk together (reordered inside);
-//   4  column-blocked scratch with natural row order (first pass of a natural two-pass).
+//   4  column-blocked scratch with natural row order (first pass of a natural two-pass);
+//   6  the head of the Haar-Walsh transform (eq. (4)): positions [0, 2^M) of a signal of
+//      Haar coefficients hold the scales k = 0..M-1 at [2^k, 2^{k+1}), each transformed by
+//      its own H_k.  The tile runs the 2^M-point cascade with the pairs that belong to
+//      stage 0 (no label bit above the butterfly bit) skipped, which leaves exactly the
+//      per-scale transforms; dyadic staged position o (o != 0) is scale
+//      k = M-1-ctz(o), entry o >> (ctz(o)+1), stored at 2^k + (o >> (ctz(o)+1)).
 #pragma once
 
 #include "engine.cuh"
@@ -46,6 +52,9 @@ struct FusedArgs {
   int colblock_a;            // OUTMODE 1, 4: rows per signal = 2^colblock_a
   int order_m;               // OUTMODE 3: bits of a signal (sequency order is per signal)
   int nat_b;                 // OUTMODE 2, column tiles: the first pass's bits (row stride 2^b)
+  int head_end;              // OUTMODE 6: scale scale k by fp32(2^{-k/2}) on output (END)
+  int64_t unit_stride;       // unit u's elements start at unit_base + u * unit_stride
+  int64_t unit_base;         //   (0 = the default: units back to back, 2^(TB+CB) apart)
 };
 
 // ------------------------------------------------------------------ phase plans
@@ -314,7 +323,8 @@ struct FusedCfg {
   static constexpr uint32_t LMASK = (1u << TB) - 1u;
   static_assert(TB >= 11 && TB <= 15, "tile must hold 64 values x 32 lanes x >=1 warp");
   static_assert(TLO == 0 || TLO == 5, "transform starts at label bit 0 (rows) or 5 (columns)");
-  static_assert(OM >= 0 && OM <= 4, "output modes 0..4");
+  static_assert((OM >= 0 && OM <= 4) || OM == 6, "output modes 0..4 and 6");
+  static_assert(OM != 6 || (TLO == 0 && CB == 0), "the Haar-Walsh head is a single-CTA row tile");
   static_assert(!natural_mode(OM) || CB == 0, "natural order is staged by single-CTA tiles");
   static_assert(OM != 4 || TLO == 0, "mode 4 is a first (row) pass");
   static_assert(CB == 0 || TLO + M == NB, "a cluster tile holds exactly one transform");
@@ -403,6 +413,21 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
       const int64_t sig = blk >> (b - 5), cb = blk & ((int64_t{1} << (b - 5)) - 1);
       const int64_t R = (og >> 5) & ((int64_t{1} << M) - 1);
       addr = (sig << (M + b)) + (R << b) + (cb << 5) + (og & 31);
+    } else if constexpr (OUTMODE == 6) {
+      // Haar-Walsh head: each element goes to its scale's block
+      uint32_t e[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int64_t qe = (og + t) & ((int64_t{1} << M) - 1);  // position within the signal
+        int64_t pos = 0;
+        if (qe != 0) {
+          const int c = __ffsll(qe) - 1;
+          pos = (int64_t{1} << (M - 1 - c)) | (qe >> (c + 1));
+          if (args.head_end) e[t] = __float_as_uint(__fmul_rn(__uint_as_float(e[t]), end_scale_dev(M - 1 - c)));
+        }
+        out[(og + t) - qe + pos] = e[t];
+      }
+      continue;
     } else {
       // sequency: dyadic position p = 4h + e (within the signal) goes to gray^{-1}(p)
       // = 4 gray^{-1}(h) + (e-th entry of {0,1,3,2}, or of {3,2,0,1} when h has odd parity)
@@ -439,7 +464,17 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
 // Phases 1 and 2 of a tile in `buf` (TMA complete): on return v holds phase 2's values and
 // no thread reads `buf` any more once the caller has synchronised.  Only for tiles that
 // have a third phase.
-template <int TLO, int M, int TB, int CB, class BF>
+// Butterflies of a phase; masked for the Haar-Walsh head when HM > 0.
+template <Phase P, int LO, int HI, int HM, class BF>
+__device__ __forceinline__ void bfly(uint32_t (&v)[64], const BF& bf, uint32_t lane, uint32_t warp) {
+  if constexpr (HM > 0) {
+    butterflies_head<P, LO, HI, HM>(v, bf, thread_label<P>(lane, warp, 0));
+  } else {
+    butterflies<P, LO, HI>(v, bf);
+  }
+}
+
+template <int TLO, int M, int TB, int CB, class BF, int HM = 0>
 __device__ __forceinline__ void phases_1_2(uint32_t (&v)[64], int64_t in_elem0, const FusedArgs& args, uint32_t* buf,
                                            const BF& bf) {
   using Cfg = FusedCfg<TLO, M, TB, CB>;
@@ -460,12 +495,12 @@ __device__ __forceinline__ void phases_1_2(uint32_t (&v)[64], int64_t in_elem0, 
         if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
       });
     }
-    butterflies<P1, 0, 5>(v, bf);
+    bfly<P1, 0, 5, HM>(v, bf, lane, warp);
     store_phase<P1, P1, LS, LMASK>(v, buf, base);
     __syncthreads();
   }
   load_phase<P2, LS, LMASK>(v, buf, thread_pos<P2, LS, LMASK>(lane, warp, 0));
-  butterflies<P2, (TLO > 5 ? TLO : 5), 11>(v, bf);
+  bfly<P2, (TLO > 5 ? TLO : 5), 11, HM>(v, bf, lane, warp);
 }
 
 // Push phase 2's values of a cluster tile to the CTAs that finish them (16-byte DSMEM
@@ -521,6 +556,7 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
   constexpr uint32_t LMASK = Cfg::LMASK;
   constexpr Phase P1 = F.p1, P2 = F.p2, P3 = F.p3, FW = F.fw;
   constexpr Lin LS = F.lin_s, LB = F.lin_b, LF = F.lin_final;
+  constexpr int HM = OUTMODE == 6 ? M : 0;
 
   const uint32_t tid = threadIdx.x;
   const uint32_t lane = tid & 31u, warp = tid >> 5;
@@ -540,12 +576,12 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
   };
 
   if constexpr (F.has_p3) {
-    phases_1_2<TLO, M, TB, CB, BF>(v, in_elem0, args, buf, bf);
+    phases_1_2<TLO, M, TB, CB, BF, HM>(v, in_elem0, args, buf, bf);
     if constexpr (!F.b_is_s) __syncthreads();
     store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
     __syncthreads();
     load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, 0));
-    butterflies<P3, 11, TLO + M>(v, bf);
+    bfly<P3, 11, TLO + M, HM>(v, bf, lane, warp);
     scale_all();
     __syncthreads();
     store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
@@ -561,7 +597,7 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
         if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
       });
     }
-    butterflies<P1, 0, (TLO + M < 5 ? TLO + M : 5)>(v, bf);
+    bfly<P1, 0, (TLO + M < 5 ? TLO + M : 5), HM>(v, bf, lane, warp);
     if constexpr (F.p1_final) {
       scale_all();
       __syncthreads();
@@ -571,7 +607,7 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
       store_phase<P1, P1, LS, LMASK>(v, buf, base);
       __syncthreads();
       load_phase<P2, LS, LMASK>(v, buf, thread_pos<P2, LS, LMASK>(lane, warp, 0));
-      butterflies<P2, 5, TLO + M>(v, bf);
+      bfly<P2, 5, TLO + M, HM>(v, bf, lane, warp);
       scale_all();
       __syncthreads();
       store_phase<FW, P2, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
@@ -630,7 +666,9 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
   __syncthreads();
   const int64_t stride = gridDim.x;
   const int64_t first = blockIdx.x;
-  auto row0 = [&](int64_t u) { return static_cast<int>(u << (TB - 5)); };
+  const int64_t ustride = args.unit_stride != 0 ? args.unit_stride : (int64_t{1} << TB);
+  auto elem0 = [&](int64_t u) { return args.unit_base + u * ustride; };
+  auto row0 = [&](int64_t u) { return static_cast<int>(elem0(u) >> 5); };
   if (threadIdx.x == 0 && first < units) tile_issue<TB>(&tin, row0(first), buf0, bar);
   int k = 0;
   for (int64_t u = first; u < units; u += stride, ++k) {
@@ -638,8 +676,7 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
     uint32_t* nxt = (k & 1) ? buf0 : buf1;
     const int64_t un = u + stride;
     if (threadIdx.x == 0 && un < units) tile_issue<TB>(&tin, row0(un), nxt, bar + ((k + 1) & 1));
-    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(static_cast<int64_t>(row0(u)) * 32, u << TB, args, cur,
-                                                     bar + (k & 1), (k >> 1) & 1);
+    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(elem0(u), elem0(u), args, cur, bar + (k & 1), (k >> 1) & 1);
     __syncthreads();
   }
 }
@@ -691,7 +728,9 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
   const int64_t first = blockIdx.x >> CB;
   const int64_t K = first < units ? (units - first + stride - 1) / stride : 0;
   auto buf = [&](int64_t i) { return bufs + (i % kClusterBufs) * (int64_t{1} << TB); };  // S_i; R_{i+1}
-  auto row0 = [&](int64_t k) { return static_cast<int>((((first + k * stride) << CB) | rank) << (TB - 5)); };
+  const int64_t ustride = args.unit_stride != 0 ? args.unit_stride : (int64_t{1} << (TB + CB));
+  auto elem0 = [&](int64_t k) { return args.unit_base + (first + k * stride) * ustride; };  // unit of iteration k
+  auto row0 = [&](int64_t k) { return static_cast<int>((elem0(k) + (int64_t{rank} << TB)) >> 5); };
   auto par = [](int64_t u) { return static_cast<uint32_t>((u / kClusterBufs) & 1); };
   BF bf{};
   if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
@@ -719,7 +758,7 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
       // ---- finish unit k-1: its pushes R_{k-1} sit in buffer (k-2) mod 3
       const int64_t u = k - 1;
       wait_cluster(fullb + u % kClusterBufs, par(u));
-      phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>((first + u * stride) << (TB + CB), args, buf(u + 2), rank, bf);
+      phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>(elem0(u), args, buf(u + 2), rank, bf);
       __syncthreads();  // buffer (k+1) mod 3 is free: the copy-out has read it
       if (tid == 0 && k + 1 < K) tile_issue<TB>(&tin, row0(k + 1), buf(k + 1), tma + (k + 1) % kClusterBufs);
     }
