@@ -285,14 +285,38 @@ def workload_config():
 
 
 # ---------------------------------------------------------------- extra configurations
+def oracle_beside(fn, nbytes, budget=0.5):
+    """The oracle as it stands, timed on a small host sample of a row's workload: repeats
+    fn() until `budget` seconds have passed; returns GB/s counting `nbytes` per call."""
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        fn()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget:
+            return round(gbs(nbytes * reps, el), 4)
+
+
 def extra_measurements(chw, torch, dev, steps, warmup, peak):
-    """Device-timed throughput of the other benchmark shapes (inputs drawn on the device)."""
+    """Device-timed throughput of the other benchmark shapes (inputs drawn on the device),
+    each with the CPU oracle timed beside it on a small sample of the same workload
+    ("cpu_oracle_GB/s", one host core, sample named in "cpu_oracle_sample")."""
+    import oracle as O
+    from paper_1609_06641_gb300 import workloads as W
+
     out = {}
 
-    def rec(name, nbytes, ms, launches, **kw):
+    def rec(name, nbytes, ms, launches, oracle=None, **kw):
         v = gbs(nbytes, ms / 1e3)
         out[name] = {"GB/s": round(v, 1), "frac_of_peak": round(v / peak, 4), "ms_per_call": round(ms, 4),
                      "launches_per_call": launches, **kw}
+        if oracle is not None:
+            fn, sample_bytes, what = oracle
+            out[name]["cpu_oracle_GB/s"] = oracle_beside(fn, sample_bytes)
+            out[name]["cpu_oracle_sample"] = what
+
+    h16 = W.normal_f32(M, 2, 11)  # two host signals of the headline shape for the oracle samples
+    nb16 = 2 * h16.nbytes
 
     st = torch.cuda.current_stream()
     g = torch.Generator(device=dev).manual_seed(7)
@@ -302,12 +326,16 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     y = torch.empty_like(x)
     p = chw.chw_plan(M, BATCH, "f32", "per_level")
     ms = time_device(lambda: chw.chw_forward(p, x, y), k, warmup, 1, st)
-    rec("m16_b4096_f32_per_level", 2 * x.numel() * 4, ms, 1)
+    rec("m16_b4096_f32_per_level", 2 * x.numel() * 4, ms, 1,
+        oracle=(lambda: O.chw_cascade(h16, M, np.float32, "per_level"), nb16, "2 signals, fp32 cascade (O4)"))
     xi = torch.randint(-(2**14), 2**14 + 1, (BATCH, 1 << M), device=dev, dtype=torch.int32, generator=g)
     yi = torch.empty_like(xi)
     pi = chw.chw_plan(M, BATCH, "i32", "none")
     ms = time_device(lambda: chw.chw_forward(pi, xi, yi), k, warmup, 1, st)
-    rec("m16_b4096_i32", 2 * xi.numel() * 4, ms, 1)
+    hi = W.uniform_int32(M, 2, 12)
+    rec("m16_b4096_i32", 2 * xi.numel() * 4, ms, 1,
+        oracle=(lambda: O.wht_fast_dyadic(hi.astype(np.int64), M, normalised=False), 2 * hi.nbytes,
+                "2 signals, int64 fast WHT (O2)"))
     del xi, yi
     # long signals: two HBM passes
     for m, b in ((26, 4), (28, 1)):
@@ -326,7 +354,10 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
         eo = torch.empty_like(ei)
         pq = chw.chw_plan(12, 16384, fmt, "end")
         ms = time_device(lambda: chw.chw_forward(pq, xq, yq, ei, eo), k, warmup, 1, st)
-        rec(f"m12_b16384_{fmt}", 2 * xq.numel() * 2, ms, 1)
+        cq, eq = W.quantise_pow2(W.heavy_tailed_f64(12, 16, 16), fmt)
+        rec(f"m12_b16384_{fmt}", 2 * xq.numel() * 2, ms, 1,
+            oracle=(lambda: O.lowp_forward_reference(cq, eq, 12, fmt, "end"), 2 * cq.nbytes,
+                    "16 signals, fp32 cascade of the codes + exponent rule"))
         del xq, yq
     # D H_m layer, m = 14, batch 512: forward and adjoint
     xd = torch.randn(512, 1 << 14, device=dev, generator=g)
@@ -334,7 +365,10 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     d = (1 - 2 * torch.randint(0, 2, (1 << 14,), device=dev, generator=g)).to(torch.int8)
     pd = chw.chw_plan(14, 512, "f32", "end")
     ms = time_device(lambda: chw.chw_forward(pd, xd, yd, diag=d), k, warmup, 1, st)
-    rec("m14_b512_DH_forward", 2 * xd.numel() * 4, ms, 1)
+    hd = W.normal_f32(14, 8, 13)
+    dd = W.diag_pm1(14, 14)
+    rec("m14_b512_DH_forward", 2 * xd.numel() * 4, ms, 1,
+        oracle=(lambda: dd * O.wht_fast_dyadic(hd.astype(np.float64), 14), 2 * hd.nbytes, "8 signals, FP64 O2 then D"))
     ms = time_device(lambda: chw.chw_adjoint(pd, yd, xd, diag=d), k, warmup, 1, st)
     rec("m14_b512_DH_adjoint", 2 * xd.numel() * 4, ms, 1)
     del xd, yd
@@ -346,13 +380,18 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     ph = chw.chw_plan(M, BATCH, "f32", "per_level", chw.CHW_FLAG_HAAR_WALSH)
     nb = xh.numel() * 4
     ms = time_device(lambda: chw.chw_haar(ph, xh, zh), k, warmup, 1, st)
-    rec("m16_b4096_f32_haar", 2 * nb, ms, 2)
+    rec("m16_b4096_f32_haar", 2 * nb, ms, 2,
+        oracle=(lambda: O.haar_forward(h16, M, np.float32, "per_level"), nb16, "2 signals, fp32 Haar (eq. (2))"))
     ms = time_device(lambda: chw.chw_haar_inverse(ph, zh, yh), k, warmup, 1, st)
-    rec("m16_b4096_f32_haar_inverse", 2 * nb, ms, 2)
+    rec("m16_b4096_f32_haar_inverse", 2 * nb, ms, 2,
+        oracle=(lambda: O.haar_inverse(h16, M, np.float32, "per_level"), nb16, "2 signals, fp32 inverse Haar"))
     ms = time_device(lambda: chw.chw_from_haar(ph, zh, yh), k, warmup, 1, st)
-    rec("m16_b4096_f32_haar_walsh", 2 * nb, ms, 1)
+    rec("m16_b4096_f32_haar_walsh", 2 * nb, ms, 1,
+        oracle=(lambda: O.haar_walsh(h16, M, np.float32, "per_level"), nb16, "2 signals, fp32 stages 1..m-1"))
     ms = time_device(lambda: chw.chw_forward_haar(ph, xh, yh, zh), k, warmup, 1, st)
-    rec("m16_b4096_f32_forward_with_haar_output", 3 * nb, ms, 3)
+    rec("m16_b4096_f32_forward_with_haar_output", 3 * nb, ms, 3,
+        oracle=(lambda: O.haar_walsh(O.haar_forward(h16, M, np.float32, "per_level"), M, np.float32, "per_level"),
+                3 * h16.nbytes, "2 signals, fp32 Haar then stages 1..m-1"))
     del xh, zh, yh, ph
     # natural and sequency output orders on the headline shape and at m = 12
     for order in ("natural", "sequency"):
@@ -362,7 +401,10 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
             po = chw.chw_plan(m, b, "f32", "end", order=order)
             info = chw.chw_plan_get_info(po)
             ms = time_device(lambda: chw.chw_forward(po, xo, yo), k, warmup, 1, st)
-            rec(f"m{m}_b{b}_f32_{order}", 2 * xo.numel() * 4, ms, info.kernels_per_call, tier=int(info.tier))
+            ho = W.normal_f32(m, 2, 15)
+            rec(f"m{m}_b{b}_f32_{order}", 2 * xo.numel() * 4, ms, info.kernels_per_call, tier=int(info.tier),
+                oracle=(lambda: O.wht_ordered(ho, m, order, np.float32, "end"), 2 * ho.nbytes,
+                        "2 signals, fp32 cascade stored in order"))
             del xo, yo, po
     # ragged: 10,000 signals with m uniform on 6..20 (seed 5), one graph launch
     from paper_1609_06641_gb300 import workloads as W
@@ -374,7 +416,11 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     yr = torch.empty_like(xr)
     ms = time_device(lambda: chw.chw_forward_ragged(pr, xr, yr), k, warmup, 1, st)
     useful = int(sum(1 << int(m) for m in ms_arr))
-    rec("ragged_10000_m6to20_f32", 2 * useful * 4, ms, 1, elements=useful)
+    rsel = [i for i in range(len(ms_arr)) if i % 250 == 0][:40]
+    hr = [W.normal_f32(int(ms_arr[i]), 1, 17 + i) for i in rsel]
+    rec("ragged_10000_m6to20_f32", 2 * useful * 4, ms, 1, elements=useful,
+        oracle=(lambda: [O.wht_fast_dyadic(h.astype(np.float64), int(ms_arr[i])) for h, i in zip(hr, rsel)],
+                sum(2 * h.nbytes for h in hr), "every 250th signal of the batch, FP64 O2"))
     return out
 
 
