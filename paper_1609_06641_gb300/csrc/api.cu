@@ -25,7 +25,8 @@ using RowstackLaunchFn = cudaError_t (*)(const CUtensorMap*, const FusedArgs&, u
                                          cudaStream_t);
 RowstackLaunchFn lookup_rowstack(int m, int var);
 int64_t haar_scratch_words(int m, int64_t batch);
-cudaError_t haar_forward(int var, int m, int64_t batch, const void* x, void* z, uint32_t* scratch, cudaStream_t st);
+cudaError_t haar_forward(int var, int m, int64_t batch, const void* x, void* z, uint32_t* scratch, int* status,
+                         cudaStream_t st);
 cudaError_t haar_inverse(int var, int m, int64_t batch, const void* z, void* x, uint32_t* scratch, cudaStream_t st);
 }  // namespace chw
 
@@ -851,7 +852,7 @@ chw_status_t chw_haar(chw_plan_t p, const void* x, void* z, void* stream) {
   chw_status_t r = check_haar_call(p, x, z, "x", "z");
   if (r != CHW_OK) return r;
   if (overlaps(x, z, static_cast<size_t>(p->total) * 4)) return fail(CHW_ERR_INVALID_ARG, "x and z overlap");
-  CHW_CUDA(chw::haar_forward(fused_variant(p, true), p->m, p->batch, x, z, p->haar_ws,
+  CHW_CUDA(chw::haar_forward(fused_variant(p, true), p->m, p->batch, x, z, p->haar_ws, p->d_status,
                              static_cast<cudaStream_t>(stream)));
   return CHW_OK;
 }

@@ -1,4 +1,6 @@
 // Launchers of the Haar analysis and synthesis passes (see haar.cuh).
+#include <cudaTypedefs.h>
+
 #include "haar.cuh"
 #include "launch.cuh"
 
@@ -6,8 +8,46 @@ namespace chw {
 
 namespace {
 
+// `words` 4-byte words at `ptr` as rows of 32 words, boxes of 256 rows (one 2^13 row of
+// the Haar passes), SWIZZLE_128B.
+bool haar_rows_map(CUtensorMap* map, const void* ptr, int64_t words) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {32, static_cast<cuuint64_t>(words / 32)};
+  cuuint64_t strides[1] = {128};
+  cuuint32_t box[2] = {32, 256};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class BF, bool END>
+cudaError_t fwd_rows(const HaarFwdArgs& a, cudaStream_t st) {
+  CUtensorMap map;
+  if (!haar_rows_map(&map, a.in, a.rows << kHaarRowBits)) return cudaErrorInvalidValue;
+  haar_fwd_row_kernel<BF, END><<<static_cast<unsigned>(a.rows), kHaarThreads, 0, st>>>(map, a);
+  return cudaGetLastError();
+}
+
+template <class BF, bool END>
+cudaError_t inv_rows(const HaarInvArgs& a, cudaStream_t st) {
+  CUtensorMap map;
+  if (!haar_rows_map(&map, a.out, a.rows << kHaarRowBits)) return cudaErrorInvalidValue;
+  haar_inv_row_kernel<BF, END><<<static_cast<unsigned>(a.rows), kHaarThreads, 0, st>>>(map, a);
+  return cudaGetLastError();
+}
+
 template <class BF, bool END>
 cudaError_t fwd_pass(const HaarFwdArgs& a, cudaStream_t st) {
+  if (a.tc == kHaarRowBits) return fwd_rows<BF, END>(a, st);
   const int64_t per_cta = int64_t{1} << (kHaarRowBits - a.tc);
   const int64_t grid = (a.rows + per_cta - 1) / per_cta;
   haar_fwd_kernel<BF, END><<<static_cast<unsigned>(grid), kHaarThreads, 0, st>>>(a);
@@ -16,6 +56,7 @@ cudaError_t fwd_pass(const HaarFwdArgs& a, cudaStream_t st) {
 
 template <class BF, bool END>
 cudaError_t inv_pass(const HaarInvArgs& a, cudaStream_t st) {
+  if (a.tc == kHaarRowBits) return inv_rows<BF, END>(a, st);
   const int64_t per_cta = int64_t{1} << (kHaarRowBits - a.tc);
   const int64_t grid = (a.rows + per_cta - 1) / per_cta;
   haar_inv_kernel<BF, END><<<static_cast<unsigned>(grid), kHaarThreads, 0, st>>>(a);
@@ -36,7 +77,8 @@ int64_t haar_scratch_words(int m, int64_t batch) {
 }
 
 // z = Psi_m x for `batch` signals (variant: kVarPerLevel, kVarEnd, kVarPlain, kVarI32).
-cudaError_t haar_forward(int var, int m, int64_t batch, const void* x, void* z, uint32_t* scratch, cudaStream_t st) {
+cudaError_t haar_forward(int var, int m, int64_t batch, const void* x, void* z, uint32_t* scratch, int* status,
+                         cudaStream_t st) {
   const int P = haar_passes(m);
   uint32_t* approx[4] = {};
   int64_t off = 0;
@@ -55,6 +97,7 @@ cudaError_t haar_forward(int var, int m, int64_t batch, const void* x, void* z, 
     a.out_stride = int64_t{1} << m;
     a.approx = p + 1 < P ? approx[p + 1] : nullptr;
     a.rows = batch << (a.mlen - a.tc);
+    a.status = status;
     cudaError_t e = cudaSuccess;
     switch (var) {
       case kVarPerLevel: e = fwd_pass<BfF32PerLevel, false>(a, st); break;
