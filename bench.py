@@ -437,6 +437,8 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="transform bits of the timed workload")
     ap.add_argument("--batch", type=int, default=BATCH, help="signals of the timed workload")
     ap.add_argument("--flags", type=int, default=0, help="chw_plan flags (e.g. 4: row-stack tier for m = 15..17)")
+    ap.add_argument("--op", default="forward", choices=["forward", "haar", "haar_inverse", "haar_walsh"],
+                    help="with --quick: the call timed (profiling runs of the other kernels)")
     args = ap.parse_args()
     world, rank, local = dist_env()
 
@@ -472,18 +474,21 @@ def main():
     x_host = W.normal_f32(m, batch, SEED + rank)  # each rank its own signals
     x = torch.from_numpy(x_host).to(dev)
     y = torch.empty_like(x)
-    plan = chw.chw_plan(m, batch, "f32", "end", args.flags)
+    flags = args.flags | (chw.CHW_FLAG_HAAR_WALSH if args.op == "haar_walsh" else 0)
+    plan = chw.chw_plan(m, batch, "f32", "end", flags)
     info = chw.chw_plan_get_info(plan)
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
-    ms = time_device(lambda: chw.chw_forward(plan, x, y), args.steps, args.warmup, world, stream, sampler)
+    call = {"forward": chw.chw_forward, "haar": chw.chw_haar, "haar_inverse": chw.chw_haar_inverse,
+            "haar_walsh": chw.chw_from_haar}[args.op if args.quick else "forward"]
+    ms = time_device(lambda: call(plan, x, y), args.steps, args.warmup, world, stream, sampler)
     ms_max = max_over_ranks(ms, world, dev)
     step_bytes = 2 * batch * (1 << m) * 4
     value = world * gbs(step_bytes, ms_max / 1e3)
     assert chw.chw_last_device_status(plan) == 0
     if args.quick:
         if rank == 0:
-            print(json.dumps({"m": m, "batch": batch, "ms_per_step": ms_max, "GB/s": value,
+            print(json.dumps({"op": args.op, "m": m, "batch": batch, "ms_per_step": ms_max, "GB/s": value,
                               "frac": value / world / peak, "clocks": sampler.summary()}), flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
