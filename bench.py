@@ -386,10 +386,10 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     rec("m16_b4096_f32_haar_inverse", 2 * nb, ms, 2,
         oracle=(lambda: O.haar_inverse(h16, M, np.float32, "per_level"), nb16, "2 signals, fp32 inverse Haar"))
     ms = time_device(lambda: chw.chw_from_haar(ph, zh, yh), k, warmup, 1, st)
-    rec("m16_b4096_f32_haar_walsh", 2 * nb, ms, 1,
+    rec("m16_b4096_f32_haar_walsh", 2 * nb, ms, 3,
         oracle=(lambda: O.haar_walsh(h16, M, np.float32, "per_level"), nb16, "2 signals, fp32 stages 1..m-1"))
     ms = time_device(lambda: chw.chw_forward_haar(ph, xh, yh, zh), k, warmup, 1, st)
-    rec("m16_b4096_f32_forward_with_haar_output", 3 * nb, ms, 3,
+    rec("m16_b4096_f32_forward_with_haar_output", 3 * nb, ms, 5,
         oracle=(lambda: O.haar_walsh(O.haar_forward(h16, M, np.float32, "per_level"), M, np.float32, "per_level"),
                 3 * h16.nbytes, "2 signals, fp32 Haar then stages 1..m-1"))
     del xh, zh, yh, ph
