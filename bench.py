@@ -416,6 +416,20 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     yr = torch.empty_like(xr)
     ms = time_device(lambda: chw.chw_forward_ragged(pr, xr, yr), k, warmup, 1, st)
     useful = int(sum(1 << int(m) for m in ms_arr))
+    # the same signals as one batched launch per length (grouped by m, no ragged kernel)
+    groups = []
+    for mm in sorted(set(int(v) for v in ms_arr)):
+        cnt = int((ms_arr == mm).sum())
+        xg = torch.randn(cnt, 1 << mm, device=dev, generator=g)
+        groups.append((chw.chw_plan(mm, cnt, "f32", "end"), xg, torch.empty_like(xg)))
+
+    def per_m():
+        for pg, xg, yg in groups:
+            chw.chw_forward(pg, xg, yg)
+
+    ms_pm = time_device(per_m, k, warmup, 1, st)
+    rec("ragged_10000_as_per_m_launches", 2 * useful * 4, ms_pm, len(groups))
+    del groups
     rsel = [i for i in range(len(ms_arr)) if i % 250 == 0][:40]
     hr = [W.normal_f32(int(ms_arr[i]), 1, 17 + i) for i in rsel]
     rec("ragged_10000_m6to20_f32", 2 * useful * 4, ms, 1, elements=useful,
