@@ -433,6 +433,7 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     rsel = [i for i in range(len(ms_arr)) if i % 250 == 0][:40]
     hr = [W.normal_f32(int(ms_arr[i]), 1, 17 + i) for i in rsel]
     rec("ragged_10000_m6to20_f32", 2 * useful * 4, ms, 1, elements=useful,
+        kernels_in_graph=int(chw.chw_plan_get_info(pr).kernels_per_call),
         oracle=(lambda: [O.wht_fast_dyadic(h.astype(np.float64), int(ms_arr[i])) for h, i in zip(hr, rsel)],
                 sum(2 * h.nbytes for h in hr), "every 250th signal of the batch, FP64 O2"))
     return out

@@ -128,8 +128,11 @@ chw_status_t chw_plan(chw_plan_t* plan, int m, int64_t batch, chw_dtype_t dtype,
  *             with m >= 5 therefore pack back to back (chw_ragged_offsets() returns the
  *             offsets; the padding elements are neither read into results nor written).
  *   dtype     CHW_F32 or CHW_I32 (with norm as for chw_plan).
- * The plan builds its task table and device work queue once; chw_forward_ragged() then
- * runs every signal in one persistent launch, replayed from a CUDA graph.
+ * The plan sorts the signals by length once and records one launch per length present
+ * (signals up to 2^12 share one persistent kernel over a work list; 2^13..2^17 run as
+ * batched one-pass launches and 2^18..2^20 as two-pass launches, reading and writing each
+ * signal at its own offset); chw_forward_ragged() replays them as one CUDA graph launch.
+ * chw_plan_get_info() reports the kernels in the graph (kernels_per_call).
  */
 chw_status_t chw_plan_ragged(chw_plan_t* plan, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,
                              chw_norm_t norm, uint32_t flags);

@@ -112,8 +112,7 @@ def _generate():
     for v in ALL:
         files[f"ragged_{v}.cu"] = (
             '#include "ragged_kernel.cuh"\n'
-            f"template cudaError_t chw::launch_ragged< ::chw::{v}>"
-            "(const CUtensorMap&, const CUtensorMap&, const ::chw::RaggedArgs&, cudaStream_t);\n"
+            f"template cudaError_t chw::launch_ragged_small< ::chw::{v}>(const ::chw::RaggedArgs&, cudaStream_t);\n"
         )
     paths = []
     for name, body in files.items():

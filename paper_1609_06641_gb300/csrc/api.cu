@@ -710,7 +710,7 @@ chw_status_t chw_plan_get_info(chw_plan_t p, chw_plan_info_t* info) {
   info->total_elements = p->total;
   info->order = p->order;
   if (p->ragged) {
-    info->kernels_per_call = 1;
+    info->kernels_per_call = chw::ragged_launches(p->ragged);  // all replayed by one graph launch
     info->workspace_bytes = static_cast<int64_t>(chw::ragged_workspace_bytes(p->ragged));
   }
   return CHW_OK;

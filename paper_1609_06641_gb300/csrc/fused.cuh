@@ -55,7 +55,21 @@ struct FusedArgs {
   int head_end;              // OUTMODE 6: scale scale k by fp32(2^{-k/2}) on output (END)
   int64_t unit_stride;       // unit u's elements start at unit_base + u * unit_stride
   int64_t unit_base;         //   (0 = the default: units back to back, 2^(TB+CB) apart)
+  // Signals at arbitrary offsets (ragged batches): when set, unit u belongs to signal
+  // u >> sig_shift and starts 2^(TB+CB) * (u mod 2^sig_shift) elements into it, the
+  // signal starting at in_off[] in the input and at out_off[] in the output.
+  const int64_t* in_off;
+  const int64_t* out_off;
+  int sig_shift;
 };
+
+// Element where unit u's input (or output) starts: from a per-signal offset table when
+// one is given, else from the unit stride.
+template <int UB>
+__device__ __forceinline__ int64_t unit_elem(const FusedArgs& a, const int64_t* off, int64_t u) {
+  if (off != nullptr) return off[u >> a.sig_shift] + ((u & ((int64_t{1} << a.sig_shift) - 1)) << UB);
+  return a.unit_base + u * (a.unit_stride != 0 ? a.unit_stride : (int64_t{1} << UB));
+}
 
 // ------------------------------------------------------------------ phase plans
 struct FusedPlan {
@@ -666,8 +680,7 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
   __syncthreads();
   const int64_t stride = gridDim.x;
   const int64_t first = blockIdx.x;
-  const int64_t ustride = args.unit_stride != 0 ? args.unit_stride : (int64_t{1} << TB);
-  auto elem0 = [&](int64_t u) { return args.unit_base + u * ustride; };
+  auto elem0 = [&](int64_t u) { return unit_elem<TB>(args, args.in_off, u); };
   auto row0 = [&](int64_t u) { return static_cast<int>(elem0(u) >> 5); };
   if (threadIdx.x == 0 && first < units) tile_issue<TB>(&tin, row0(first), buf0, bar);
   int k = 0;
@@ -676,7 +689,8 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
     uint32_t* nxt = (k & 1) ? buf0 : buf1;
     const int64_t un = u + stride;
     if (threadIdx.x == 0 && un < units) tile_issue<TB>(&tin, row0(un), nxt, bar + ((k + 1) & 1));
-    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(elem0(u), elem0(u), args, cur, bar + (k & 1), (k >> 1) & 1);
+    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(elem0(u), unit_elem<TB>(args, args.out_off, u), args, cur,
+                                                     bar + (k & 1), (k >> 1) & 1);
     __syncthreads();
   }
 }
@@ -728,8 +742,9 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
   const int64_t first = blockIdx.x >> CB;
   const int64_t K = first < units ? (units - first + stride - 1) / stride : 0;
   auto buf = [&](int64_t i) { return bufs + (i % kClusterBufs) * (int64_t{1} << TB); };  // S_i; R_{i+1}
-  const int64_t ustride = args.unit_stride != 0 ? args.unit_stride : (int64_t{1} << (TB + CB));
-  auto elem0 = [&](int64_t k) { return args.unit_base + (first + k * stride) * ustride; };  // unit of iteration k
+  // first input / output element of the unit of iteration k
+  auto elem0 = [&](int64_t k) { return unit_elem<TB + CB>(args, args.in_off, first + k * stride); };
+  auto oelem0 = [&](int64_t k) { return unit_elem<TB + CB>(args, args.out_off, first + k * stride); };
   auto row0 = [&](int64_t k) { return static_cast<int>((elem0(k) + (int64_t{rank} << TB)) >> 5); };
   auto par = [](int64_t u) { return static_cast<uint32_t>((u / kClusterBufs) & 1); };
   BF bf{};
@@ -758,7 +773,7 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
       // ---- finish unit k-1: its pushes R_{k-1} sit in buffer (k-2) mod 3
       const int64_t u = k - 1;
       wait_cluster(fullb + u % kClusterBufs, par(u));
-      phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>(elem0(u), args, buf(u + 2), rank, bf);
+      phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>(oelem0(u), args, buf(u + 2), rank, bf);
       __syncthreads();  // buffer (k+1) mod 3 is free: the copy-out has read it
       if (tid == 0 && k + 1 < K) tile_issue<TB>(&tin, row0(k + 1), buf(k + 1), tma + (k + 1) % kClusterBufs);
     }

@@ -1,37 +1,46 @@
-// Host side of ragged plans: packing, task table, graph capture (see ragged.cuh).
+// Host side of ragged plans: packing, grouping by length, graph capture (see ragged.cuh).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "ragged_kernel.cuh"
 
 namespace chw {
 
-// One translation unit per variant instantiates the kernel (generated by the build).
-extern template cudaError_t launch_ragged<kVarPerLevel>(const CUtensorMap&, const CUtensorMap&, const RaggedArgs&, cudaStream_t);
-extern template cudaError_t launch_ragged<kVarEnd>(const CUtensorMap&, const CUtensorMap&, const RaggedArgs&, cudaStream_t);
-extern template cudaError_t launch_ragged<kVarPlain>(const CUtensorMap&, const CUtensorMap&, const RaggedArgs&, cudaStream_t);
-extern template cudaError_t launch_ragged<kVarI32>(const CUtensorMap&, const CUtensorMap&, const RaggedArgs&, cudaStream_t);
+// One translation unit per variant instantiates the short-signal kernel (generated by the build).
+extern template cudaError_t launch_ragged_small<kVarPerLevel>(const RaggedArgs&, cudaStream_t);
+extern template cudaError_t launch_ragged_small<kVarEnd>(const RaggedArgs&, cudaStream_t);
+extern template cudaError_t launch_ragged_small<kVarPlain>(const RaggedArgs&, cudaStream_t);
+extern template cudaError_t launch_ragged_small<kVarI32>(const RaggedArgs&, cudaStream_t);
 
 // ------------------------------------------------------------------ host side
+struct RaggedGroup {
+  int m = 0;
+  int64_t count = 0;
+  int64_t* d_off = nullptr;  // the group's signal offsets (device)
+};
+
 struct RaggedPlan {
   int64_t count = 0;
   std::vector<uint8_t> ms;
   std::vector<int64_t> off;  // count + 1 entries
   int64_t total = 0;
-  int64_t map_words = 0;  // extent of the input tensor map
   int variant = 0;
   int* d_status = nullptr;
+  // short signals: a work list for the persistent kernel
   int ntasks = 0;
-  int nctr = 0;
-  int nbig = 0;
   RaggedTask* d_tasks = nullptr;
-  int32_t* d_ctrs = nullptr;  // [0] queue head, [1..] dependency counters
+  int32_t* d_head = nullptr;
   uint8_t* d_ms = nullptr;
   int64_t* d_off = nullptr;
-  uint32_t* d_ring = nullptr;
+  // longer signals: one batched launch (two per chunk for m >= 18) per length
+  std::vector<RaggedGroup> groups;
+  uint32_t* d_scratch = nullptr;
+  int64_t scratch_words = 0;
+  int launches = 0;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   const void* gx = nullptr;
@@ -44,10 +53,11 @@ void free_plan(RaggedPlan* r) {
   if (r->exec) cudaGraphExecDestroy(r->exec);
   if (r->cap) cudaStreamDestroy(r->cap);
   cudaFree(r->d_tasks);
-  cudaFree(r->d_ctrs);
+  cudaFree(r->d_head);
   cudaFree(r->d_ms);
   cudaFree(r->d_off);
-  cudaFree(r->d_ring);
+  for (RaggedGroup& g : r->groups) cudaFree(g.d_off);
+  cudaFree(r->d_scratch);
   delete r;
 }
 
@@ -68,6 +78,68 @@ bool encode_rows(CUtensorMap* map, const void* ptr, int64_t words) {
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+float end_scale_host(int m) {  // fp32(2^{-m/2}), as the kernels compute it
+  const float r = (m & 1) ? 0.70710678118654752440f : 1.0f;
+  return std::ldexp(r, -(m / 2));
+}
+
+constexpr int kTwoPassA = 9;  // column bits of the two-pass split for m = 18..20
+
+int64_t two_pass_chunk(int m) { return std::max<int64_t>(1, kRaggedScratchWords >> m); }
+
+// Record the launches of one length group on the capture stream.
+cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, const CUtensorMap& tx, const CUtensorMap& ts,
+                         void* y) {
+  cudaStream_t st = r->cap;
+  const int m = g.m;
+  if (m <= 17) {
+    const int tb = m == 13 ? 13 : 14, cb = m <= 14 ? 0 : m - 14;
+    FusedLaunchFn fn = lookup_fused(0, m, tb, cb, r->variant, 0);
+    if (!fn) return cudaErrorInvalidValue;
+    FusedArgs a{};
+    a.status = r->d_status;
+    a.out = y;
+    a.out_total = r->total;
+    a.end_scale = end_scale_host(m);
+    a.in_off = g.d_off;
+    a.out_off = g.d_off;
+    a.sig_shift = 0;
+    return fn(&tx, a, g.count, st);
+  }
+  // m = 18..20: pass 1 on rows of 2^b (2^(13-b) rows per 2^13-word tile, 2^(m-13) tiles per
+  // signal) into column-blocked scratch; pass 2 on 2^a x 32 column tiles of 2^14 words
+  // (2^(m-14) per signal) written back at the signal's offset.
+  const int A = kTwoPassA, b = m - A;
+  const int v1 = r->variant == kVarEnd ? static_cast<int>(kVarPlain) : r->variant;
+  FusedLaunchFn f1 = lookup_fused(0, b, 13, 0, v1, 1);
+  FusedLaunchFn f2 = lookup_fused(5, A, 14, 0, r->variant, 0);
+  if (!f1 || !f2) return cudaErrorInvalidValue;
+  const int64_t chunk = two_pass_chunk(m);
+  for (int64_t s0 = 0; s0 < g.count; s0 += chunk) {
+    const int64_t cnt = std::min(chunk, g.count - s0);
+    FusedArgs p1{};
+    p1.status = r->d_status;
+    p1.out = r->d_scratch;
+    p1.out_total = cnt << m;
+    p1.end_scale = 1.0f;
+    p1.colblock_a = A;
+    p1.in_off = g.d_off + s0;
+    p1.sig_shift = m - 13;
+    cudaError_t e = f1(&tx, p1, cnt << (m - 13), st);
+    if (e != cudaSuccess) return e;
+    FusedArgs p2{};
+    p2.status = r->d_status;
+    p2.out = y;
+    p2.out_total = r->total;
+    p2.end_scale = end_scale_host(m);
+    p2.out_off = g.d_off + s0;
+    p2.sig_shift = m - 14;
+    e = f2(&ts, p2, cnt << (m - 14), st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -95,71 +167,17 @@ RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t 
   r->d_status = d_status;
   r->total = total;
 
-  // ---- task table
+  // ---- short signals: runs of consecutive short signals, about 128 KiB each
   std::vector<RaggedTask> tasks;
-  std::vector<int64_t> big;
-  for (int64_t i = 0; i < count; ++i)
-    if (ms[i] > kRaggedTileBits) big.push_back(i);
-  std::stable_sort(big.begin(), big.end(), [&](int64_t a, int64_t b) { return ms[a] > ms[b]; });
-  r->nbig = static_cast<int>(big.size());
-  auto parts = [&](int64_t sig) { return 1 << (ms[sig] - kRaggedTileBits); };
-  auto emit_rows = [&](int k) {
-    const int64_t s = big[k];
-    for (int j = 0; j < parts(s); ++j) {
-      RaggedTask t{};
-      t.kind = kTaskRow;
-      t.m = ms[s];
-      t.off = r->off[s];
-      t.index = j;
-      t.slot = k % kRingSlots;
-      t.wait_on = k >= kRingSlots ? 1 + 2 * (k - kRingSlots) + 1 : -1;
-      t.wait_val = k >= kRingSlots ? parts(big[k - kRingSlots]) : 0;
-      t.done_ctr = 1 + 2 * k;
-      tasks.push_back(t);
-    }
-  };
-  auto emit_cols = [&](int k) {
-    const int64_t s = big[k];
-    for (int j = 0; j < parts(s); ++j) {
-      RaggedTask t{};
-      t.kind = kTaskCol;
-      t.m = ms[s];
-      t.off = r->off[s];
-      t.index = j;
-      t.slot = k % kRingSlots;
-      t.wait_on = 1 + 2 * k;
-      t.wait_val = parts(s);
-      t.done_ctr = 1 + 2 * k + 1;
-      tasks.push_back(t);
-    }
-  };
-  for (int k = 0; k < r->nbig; ++k) {
-    emit_rows(k);
-    if (k >= 1) emit_cols(k - 1);
-  }
-  if (r->nbig > 0) emit_cols(r->nbig - 1);
-  for (int64_t i = 0; i < count; ++i) {
-    if (ms[i] != kRaggedTileBits) continue;
-    RaggedTask t{};
-    t.kind = kTaskTile;
-    t.m = ms[i];
-    t.off = r->off[i];
-    t.wait_on = -1;
-    t.done_ctr = -1;
-    tasks.push_back(t);
-  }
   for (int64_t i = 0; i < count;) {
-    if (ms[i] >= kRaggedTileBits) {
+    if (ms[i] > kRaggedSmallMaxM) {
       ++i;
       continue;
     }
     RaggedTask t{};
-    t.kind = kTaskSmall;
     t.index = static_cast<int32_t>(i);
-    t.wait_on = -1;
-    t.done_ctr = -1;
     int64_t words = 0;
-    while (i < count && ms[i] < kRaggedTileBits && words < kSmallGroupWords) {
+    while (i < count && ms[i] <= kRaggedSmallMaxM && words < kSmallGroupWords) {
       words += int64_t{1} << ms[i];
       ++i;
       ++t.count;
@@ -167,22 +185,36 @@ RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t 
     tasks.push_back(t);
   }
   r->ntasks = static_cast<int>(tasks.size());
-  r->nctr = 1 + 2 * r->nbig;
-  // TILE/ROW/COL tasks read x through a tensor map of whole 32-word rows; without them the
-  // map is never used and one row stands in for arrays shorter than 32 words.
-  bool tma = false;
-  for (const RaggedTask& t : tasks) tma |= t.kind != kTaskSmall;
-  r->map_words = tma ? r->total : 32;
+  if (r->ntasks > 0) r->launches += 1;
 
-  cudaError_t e = cudaMalloc(&r->d_tasks, std::max<size_t>(1, tasks.size()) * sizeof(RaggedTask));
-  if (e == cudaSuccess && !tasks.empty())
-    e = cudaMemcpy(r->d_tasks, tasks.data(), tasks.size() * sizeof(RaggedTask), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&r->d_ctrs, r->nctr * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&r->d_ms, count);
-  if (e == cudaSuccess) e = cudaMemcpy(r->d_ms, ms, count, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&r->d_off, (count + 1) * sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMemcpy(r->d_off, r->off.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && r->nbig > 0) e = cudaMalloc(&r->d_ring, kRingSlots * kRingSlotWords * sizeof(uint32_t));
+  // ---- longer signals: one group per length
+  cudaError_t e = cudaSuccess;
+  for (int m = kRaggedSmallMaxM + 1; m <= kRaggedMaxM && e == cudaSuccess; ++m) {
+    std::vector<int64_t> go;
+    for (int64_t i = 0; i < count; ++i)
+      if (ms[i] == m) go.push_back(offsets[i]);
+    if (go.empty()) continue;
+    RaggedGroup g;
+    g.m = m;
+    g.count = static_cast<int64_t>(go.size());
+    e = cudaMalloc(&g.d_off, go.size() * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_off, go.data(), go.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    r->groups.push_back(g);
+    r->launches += m >= 18 ? static_cast<int>(2 * ((g.count + two_pass_chunk(m) - 1) / two_pass_chunk(m))) : 1;
+    if (m >= 18) r->scratch_words = kRaggedScratchWords;
+  }
+  if (e == cudaSuccess && r->ntasks > 0) {
+    e = cudaMalloc(&r->d_tasks, tasks.size() * sizeof(RaggedTask));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(r->d_tasks, tasks.data(), tasks.size() * sizeof(RaggedTask), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&r->d_head, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&r->d_ms, count);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_ms, ms, count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&r->d_off, (count + 1) * sizeof(int64_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(r->d_off, r->off.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && r->scratch_words > 0) e = cudaMalloc(&r->d_scratch, r->scratch_words * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     *why = cudaGetErrorString(e);
@@ -195,10 +227,9 @@ RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t 
 
 void ragged_destroy(RaggedPlan* r) { free_plan(r); }
 int64_t ragged_total(const RaggedPlan* r) { return r->total; }
-int ragged_passes(const RaggedPlan* r) { return r->nbig > 0 ? 2 : 1; }
-size_t ragged_workspace_bytes(const RaggedPlan* r) {
-  return r->nbig > 0 ? kRingSlots * kRingSlotWords * sizeof(uint32_t) : 0;
-}
+int ragged_passes(const RaggedPlan* r) { return r->scratch_words > 0 ? 2 : 1; }
+int ragged_launches(const RaggedPlan* r) { return r->launches; }
+size_t ragged_workspace_bytes(const RaggedPlan* r) { return static_cast<size_t>(r->scratch_words) * sizeof(uint32_t); }
 void ragged_offsets(const RaggedPlan* r, int64_t* out) { std::memcpy(out, r->off.data(), (r->count + 1) * sizeof(int64_t)); }
 
 int ragged_run(RaggedPlan* r, const void* x, void* y, cudaStream_t st, std::string* why) {
@@ -207,36 +238,41 @@ int ragged_run(RaggedPlan* r, const void* x, void* y, cudaStream_t st, std::stri
       cudaGraphExecDestroy(r->exec);
       r->exec = nullptr;
     }
-    CUtensorMap tx, tr;
-    if (!encode_rows(&tx, x, r->map_words) ||
-        !encode_rows(&tr, r->d_ring ? static_cast<const void*>(r->d_ring) : x,
-                     r->d_ring ? kRingSlots * kRingSlotWords : r->map_words)) {
+    // Tensor maps need whole 32-word rows; without a batched launch (short signals only) the
+    // map is never used and one row stands in for arrays shorter than 32 words.
+    const bool tma = !r->groups.empty();
+    CUtensorMap tx, ts;
+    if (!encode_rows(&tx, x, tma ? r->total : 32) ||
+        !encode_rows(&ts, r->d_scratch ? static_cast<const void*>(r->d_scratch) : x,
+                     r->d_scratch ? r->scratch_words : (tma ? r->total : 32))) {
       *why = "cuTensorMapEncodeTiled failed";
       return 1;
     }
     RaggedArgs a{};
     a.tasks = r->d_tasks;
     a.ntasks = r->ntasks;
-    a.queue_head = r->d_ctrs;
-    a.ctr = r->d_ctrs;
+    a.queue_head = r->d_head;
     a.ms = r->d_ms;
     a.off = r->d_off;
     a.x = static_cast<const uint32_t*>(x);
     a.y = static_cast<uint32_t*>(y);
-    a.ring = r->d_ring;
-    a.total = r->total;
-    a.status = r->d_status;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t le = cudaSuccess;
     if (e == cudaSuccess) {
-      cudaMemsetAsync(r->d_ctrs, 0, r->nctr * sizeof(int32_t), r->cap);
-      switch (r->variant) {
-        case kVarPerLevel: launch_ragged<kVarPerLevel>(tx, tr, a, r->cap); break;
-        case kVarEnd: launch_ragged<kVarEnd>(tx, tr, a, r->cap); break;
-        case kVarPlain: launch_ragged<kVarPlain>(tx, tr, a, r->cap); break;
-        default: launch_ragged<kVarI32>(tx, tr, a, r->cap); break;
+      if (r->ntasks > 0) {
+        cudaMemsetAsync(r->d_head, 0, sizeof(int32_t), r->cap);
+        switch (r->variant) {
+          case kVarPerLevel: le = launch_ragged_small<kVarPerLevel>(a, r->cap); break;
+          case kVarEnd: le = launch_ragged_small<kVarEnd>(a, r->cap); break;
+          case kVarPlain: le = launch_ragged_small<kVarPlain>(a, r->cap); break;
+          default: le = launch_ragged_small<kVarI32>(a, r->cap); break;
+        }
       }
+      for (const RaggedGroup& grp : r->groups)
+        if (le == cudaSuccess) le = launch_group(r, grp, tx, ts, y);
       e = cudaStreamEndCapture(r->cap, &g);
+      if (e == cudaSuccess && le != cudaSuccess) e = le;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&r->exec, g, 0);
     if (g) cudaGraphDestroy(g);
