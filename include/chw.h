@@ -76,6 +76,10 @@ typedef enum chw_norm_e {
 #define CHW_FLAG_HAAR_WALSH 8u      /* also prepare chw_from_haar / chw_forward_haar       */
 #define CHW_FLAG_ORDER_NATURAL 16u  /* store outputs in natural (Sylvester) order          */
 #define CHW_FLAG_ORDER_SEQUENCY 32u /* store outputs in sequency (Walsh) order             */
+#define CHW_FLAG_TEST_STALL 64u     /* test hook, cluster tier (m = 15..17): one CTA       */
+                                    /* withholds a signal and waits give up after a few    */
+                                    /* thousand polls, so chw_last_device_status() reports */
+                                    /* CHW_ERR_TIMEOUT; the output is then undefined       */
 
 typedef struct chw_plan_s* chw_plan_t;
 

@@ -23,6 +23,7 @@ from ._lib import (
     CHW_FLAG_ORDER_NATURAL,
     CHW_FLAG_ORDER_SEQUENCY,
     CHW_FLAG_ROWSTACK,
+    CHW_FLAG_TEST_STALL,
     CHW_FLAG_FORCE_MULTIPASS,
     CHW_FLAG_FORCE_SIMPLE,
     CHW_FLAG_NONE,

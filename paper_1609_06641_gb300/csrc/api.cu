@@ -228,6 +228,8 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
   a.colblock_a = colblock_a;
   a.order_m = M;
   a.nat_b = 0;
+  a.stall_cta = (p->flags & CHW_FLAG_TEST_STALL) != 0 ? 2 : 0;  // rank 1 withholds its signal
+  a.wait_tries = (p->flags & CHW_FLAG_TEST_STALL) != 0 ? 4096u : 0u;
   const int64_t unit = int64_t{1} << (s.tb + s.cb);
   const int64_t units = s.cb > 0 ? total / unit : (total + unit - 1) / unit;
   CHW_CUDA(fn(&map, a, units, st));

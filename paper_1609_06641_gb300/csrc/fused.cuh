@@ -61,6 +61,12 @@ struct FusedArgs {
   const int64_t* in_off;
   const int64_t* out_off;
   int sig_shift;
+  // Test hook of the cluster kernel's failure detection: the CTA of rank stall_cta - 1
+  // (0: none) withholds its first "full" signal, and waits give up after `wait_tries`
+  // polls (0: kWaitTries), so the other CTAs' bounded waits run out and report
+  // CHW_ERR_TIMEOUT while every CTA still finishes.
+  int stall_cta;
+  uint32_t wait_tries;
 };
 
 // Element where unit u's input (or output) starts: from a per-signal offset table when
@@ -693,6 +699,13 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
                                                      bar + (k & 1), (k >> 1) & 1);
     __syncthreads();
   }
+  // no TMA load left in flight into shared memory, even after a wait gave up
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2 && b < k; ++b) {
+      const int kl = b + ((k - 1 - b) / 2) * 2;  // this CTA's last unit on buffer b
+      mbar_wait_bounded(bar + b, (kl >> 1) & 1, kWaitTries);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ the cluster kernel
@@ -752,14 +765,15 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
   // A wait that gives up records CHW_ERR_TIMEOUT and turns every later wait of this thread
   // off, so a broken schedule costs one bounded wait per thread, not one per unit.
   bool waiting = true;
+  const uint32_t tries = args.wait_tries != 0 ? args.wait_tries : kWaitTries;
   auto wait_local = [&](uint64_t* b, uint32_t parity) {
-    if (waiting && !mbar_wait_bounded(b, parity, kWaitTries)) {
+    if (waiting && !mbar_wait_bounded(b, parity, tries)) {
       waiting = false;
       if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
     }
   };
   auto wait_cluster = [&](uint64_t* b, uint32_t parity) {
-    if (waiting && !mbar_wait_cluster_bounded(b, parity, kWaitTries)) {
+    if (waiting && !mbar_wait_cluster_bounded(b, parity, tries)) {
       waiting = false;
       if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
     }
@@ -787,10 +801,18 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
       wait_cluster(freeb + k % kClusterBufs, par(k));
       push_to_finishers<TLO, M, TB, CB>(v, buf(k + 2), rank);
       __syncthreads();  // every push of this CTA is issued
-      if (tid < NR) {
+      if (tid < NR && !(k == 0 && static_cast<int>(rank) + 1 == args.stall_cta)) {
         fence_acq_rel_cluster();
         mbar_remote_arrive(fullb + k % kClusterBufs, tid);
       }
+    }
+  }
+  // Leave no TMA load in flight into this CTA's shared memory, even when a wait above gave
+  // up: wait (bounded) for the last load issued on each barrier.
+  if (tid == 0) {
+    for (int64_t i = 0; i < kClusterBufs && i < K; ++i) {
+      const int64_t u = i + ((K - 1 - i) / kClusterBufs) * kClusterBufs;
+      mbar_wait_bounded(tma + i, par(u), kWaitTries);
     }
   }
   cluster_arrive();  // no CTA leaves while a peer may still push into it or signal it

@@ -335,6 +335,7 @@ __global__ void __launch_bounds__(kHaarThreads) haar_fwd_row_kernel(const __grid
       out[0] = x;
     }
   }
+  if (t == 0) mbar_wait_bounded(&bar, 0, kWaitTries);  // the row load is not in flight at exit
 }
 
 template <class BF, bool END>

@@ -219,6 +219,13 @@ __global__ void __launch_bounds__(1 << (M - 6), 6)
     }
     __syncthreads();
   }
+  // no TMA load left in flight into shared memory, even after a wait gave up
+  if (tid == 0) {
+    for (int b = 0; b < 2 && b < k; ++b) {
+      const int kl = b + ((k - 1 - b) / 2) * 2;
+      mbar_wait_bounded(bar + b, (kl >> 1) & 1, kWaitTries);
+    }
+  }
 }
 
 template <int M, bool F16, class BF, bool SCALE>
