@@ -177,7 +177,7 @@ def time_device(fn, steps, warmup, world, stream, sampler=None):
 
 
 def traffic_from_profile(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this build."""
+    """DRAM bytes per launch from the committed ncu summary, if it matches the compiled kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None

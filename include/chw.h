@@ -43,7 +43,7 @@ extern "C" {
 typedef enum chw_status_e {
   CHW_OK = 0,
   CHW_ERR_INVALID_ARG = 1,  /* bad m, batch, dtype/norm pairing, null pointer, ...   */
-  CHW_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement          */
+  CHW_ERR_UNSUPPORTED = 2,  /* valid request this library does not implement        */
   CHW_ERR_ALIGNMENT = 3,    /* a data pointer is not 16-byte aligned                 */
   CHW_ERR_OOM = 4,          /* the plan's device workspace could not be allocated    */
   CHW_ERR_CUDA = 5,         /* a CUDA runtime call failed (no device, launch error)  */

@@ -59,7 +59,11 @@ def order_permutation(m, order):
     if order == "dyadic":
         return k
     if order == "natural":
-        return np.array([bitrev(int(i), m) for i in k], dtype=np.int64)
+        # bitrev_m for every k at once: bit b of k moves to bit m-1-b
+        r = np.zeros_like(k)
+        for b in range(m):
+            r |= ((k >> b) & 1) << (m - 1 - b)
+        return r
     return k ^ (k >> 1)
 
 

@@ -622,7 +622,7 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     p->row_bits = m - a;
   } else {
     delete p;
-    return fail(CHW_ERR_UNSUPPORTED, "m=%d needs three HBM passes, which this build does not implement", m);
+    return fail(CHW_ERR_UNSUPPORTED, "m=%d needs three HBM passes, which this library does not implement", m);
   }
 
   cudaError_t e = cudaGetDevice(&p->device);

@@ -34,6 +34,12 @@ def test_sequency_matrix_definition(m):
     assert np.array_equal(seq, seq.T)
 
 
+@pytest.mark.parametrize("m", [0, 1, 5, 11])
+def test_natural_permutation_is_bitrev(m):
+    perm = O.order_permutation(m, "natural")
+    assert [int(v) for v in perm] == [O.bitrev(k, m) for k in range(1 << m)]
+
+
 def test_small_cases_by_hand():
     # m = 2: dyadic rows [1,1,1,1], [1,1,-1,-1], [1,-1,1,-1], [1,-1,-1,1] (eq. (1));
     # natural swaps the middle two, sequency orders by 0,1,2,3 sign changes
