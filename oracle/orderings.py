@@ -20,7 +20,6 @@ matrices built from their definitions, the sign-change count, symmetry).
 
 import numpy as np
 
-from .definitions import bitrev
 from .transforms import chw_cascade
 
 ORDERS = ("dyadic", "natural", "sequency")
