@@ -555,7 +555,9 @@ def main():
             "traffic": traffic_from_profile(f"m{m}_b{batch}_f32_end_tier{info.tier}"),
             "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else "fallback",
             "kernel": {2: "cluster_kernel<0,16,14,2> (4-CTA cluster per signal, DSMEM exchange)",
-                       6: "rowstack_kernel<16> (one CTA per signal, rows through L2)"}.get(info.tier, str(info.tier)),
+                       6: "rowstack_kernel<16> (one CTA per signal, rows through L2)",
+                       7: "tmem_kernel<16> (one CTA per signal, rows via shared memory, signal in tensor memory)"}
+            .get(info.tier, str(info.tier)),
         },
         "e2e": {
             "value": round(gbs(step_bytes, e2e_s) * world, 1),

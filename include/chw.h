@@ -13,7 +13,9 @@
  * every block of length 2^{m-r+1}.  The cascade's butterflies are fused into register,
  * shared-memory, cluster (DSMEM) and HBM tiers; every schedule performs the same
  * butterflies on the same operands, so results round exactly as the cascade taken in
- * the paper's stage order does.
+ * the paper's stage order does.  Signals of 2^15 and 2^16 elements are held on one SM,
+ * their rows in shared memory and the whole signal in the SM's tensor memory (tcgen05),
+ * between the row butterflies and the last ones.
  *
  * Conventions for every call below:
  *   - Pointers named x, y, exp_*, diag are DEVICE pointers unless the name says _host.
@@ -80,6 +82,8 @@ typedef enum chw_norm_e {
                                     /* withholds a signal and waits give up after a few    */
                                     /* thousand polls, so chw_last_device_status() reports */
                                     /* CHW_ERR_TIMEOUT; the output is then undefined       */
+#define CHW_FLAG_CLUSTER 128u       /* m = 15, 16: thread-block-cluster (DSMEM) tier instead */
+                                    /* of the tensor-memory tier                           */
 
 typedef struct chw_plan_s* chw_plan_t;
 
@@ -90,7 +94,8 @@ typedef struct chw_plan_info_s {
   int dtype;                 /* chw_dtype_t                                            */
   int norm;                  /* chw_norm_t                                             */
   int tier;                  /* 0 simple, 1 fused CTA, 2 fused cluster, 3 two-pass, 4 ragged,
-                                5 fused 16-bit, 6 row-stack (one CTA, L2-resident rows) */
+                                5 fused 16-bit, 6 row-stack (one CTA, L2-resident rows),
+                                7 tensor memory (one CTA per signal, m = 15, 16)        */
   int passes;                /* HBM round trips per call                               */
   int row_bits;              /* two-pass: bits transformed in pass 1 (else m)          */
   int cluster;               /* CTAs per cluster in the fused (or first) pass          */

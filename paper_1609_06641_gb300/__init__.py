@@ -19,6 +19,7 @@ from ._lib import (
     CHW_BF16,
     CHW_F16,
     CHW_F32,
+    CHW_FLAG_CLUSTER,
     CHW_FLAG_HAAR_WALSH,
     CHW_FLAG_ORDER_NATURAL,
     CHW_FLAG_ORDER_SEQUENCY,
@@ -38,7 +39,16 @@ from ._lib import (
 DTYPES = {"i32": CHW_I32, "f32": CHW_F32, "bf16": CHW_BF16, "f16": CHW_F16}
 NORMS = {"none": CHW_NORM_NONE, "per_level": CHW_NORM_PER_LEVEL, "end": CHW_NORM_END}
 ORDERS = {"dyadic": 0, "natural": CHW_FLAG_ORDER_NATURAL, "sequency": CHW_FLAG_ORDER_SEQUENCY}
-TIERS = {0: "simple", 1: "fused", 2: "cluster", 3: "two-pass", 4: "ragged", 5: "fused-16bit", 6: "row-stack"}
+TIERS = {
+    0: "simple",
+    1: "fused",
+    2: "cluster",
+    3: "two-pass",
+    4: "ragged",
+    5: "fused-16bit",
+    6: "row-stack",
+    7: "tensor-memory",
+}
 
 
 def _torch_dtype(code):

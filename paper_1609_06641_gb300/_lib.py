@@ -35,6 +35,7 @@ CHW_FLAG_HAAR_WALSH = 8
 CHW_FLAG_ORDER_NATURAL = 16
 CHW_FLAG_ORDER_SEQUENCY = 32
 CHW_FLAG_TEST_STALL = 64
+CHW_FLAG_CLUSTER = 128
 
 
 class chw_plan_info_t(ctypes.Structure):

@@ -142,10 +142,10 @@ def _digest():
     return h.hexdigest()
 
 
-# Sources of the batched single-CTA and cluster kernels (the kernels the benchmark's roofline
-# record names); recorded next to committed DRAM-traffic figures so that a figure is used
-# only while the kernel it was measured on is unchanged.
-KERNEL_SOURCES = ("ptx.cuh", "engine.cuh", "fused.cuh", "launch.cuh")
+# Sources of the batched single-CTA, cluster and tensor-memory kernels (the kernels the
+# benchmark's roofline record names); recorded next to committed DRAM-traffic figures so
+# that a figure is used only while the kernel it was measured on is unchanged.
+KERNEL_SOURCES = ("ptx.cuh", "engine.cuh", "fused.cuh", "launch.cuh", "tmem.cuh", "tmem.cu")
 
 
 def kernel_digest():

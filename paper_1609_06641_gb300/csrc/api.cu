@@ -50,7 +50,16 @@ chw_status_t fail(chw_status_t s, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(CHW_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
   } while (0)
 
-enum Tier { kTierSimple = 0, kTierFused = 1, kTierCluster = 2, kTierTwoPass = 3, kTierRagged = 4, kTierLowp = 5, kTierRowStack = 6 };
+enum Tier {
+  kTierSimple = 0,
+  kTierFused = 1,
+  kTierCluster = 2,
+  kTierTwoPass = 3,
+  kTierRagged = 4,
+  kTierLowp = 5,
+  kTierRowStack = 6,
+  kTierTmem = 7
+};
 
 struct Shape {
   int tb, cb;
@@ -236,6 +245,26 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
   return CHW_OK;
 }
 
+// Tensor-memory tier (m = 15, 16, dyadic order): one signal per SM at a time.
+chw_status_t launch_tmem_pass(chw_plan_s* p, const void* in, void* out, int64_t total, const int8_t* diag_in,
+                              const int8_t* diag_out, cudaStream_t st) {
+  chw::FusedLaunchFn fn = chw::lookup_tmem(p->m, fused_variant(p, true));
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no tensor-memory kernel for m=%d", p->m);
+  CUtensorMap map;
+  chw_status_t r = make_rows_map(&map, in, total, 14);
+  if (r != CHW_OK) return r;
+  chw::FusedArgs a{};
+  a.out = out;
+  a.out_total = total;
+  a.end_scale = end_scale_f32(p->m);
+  a.diag_in = diag_in;
+  a.diag_out = diag_out;
+  a.diag_mask = (int64_t{1} << p->m) - 1;
+  a.status = p->d_status;
+  CHW_CUDA(fn(&map, a, total >> p->m, st));
+  return CHW_OK;
+}
+
 chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, int om, const void* in, void* out, int64_t total,
                              const int8_t* diag_out, int64_t diag_mask, float scale, cudaStream_t st) {
   const Shape s = om == 2 ? Shape{A <= 8 ? 13 : 14, 0} : col_shape(A);
@@ -360,6 +389,8 @@ chw_status_t run_transform(chw_plan_s* p, const void* x, void* y, int64_t batch,
       return launch_lowp_fused(p, x, y, batch, exp_in, exp_out, diag_in, diag_out, st);
     case kTierRowStack:
       return launch_rowstack(p, x, y, batch, diag_in, diag_out, ws, p->rowstack_slots, st);
+    case kTierTmem:
+      return launch_tmem_pass(p, x, y, total, diag_in, diag_out, st);
     case kTierFused:
     case kTierCluster:
       return launch_row_pass(p, m, final_outmode(p), fused_variant(p, true), x, y, total, diag_in, diag_out, dmask,
@@ -611,7 +642,9 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     if (m < 5 && p->total % 32 != 0) {
       p->tier = kTierSimple;
     } else if (m >= 15) {
-      p->tier = (flags & CHW_FLAG_ROWSTACK) != 0 ? kTierRowStack : kTierCluster;
+      const bool tmem = m <= 16 && p->order == 0 &&
+                        (flags & (CHW_FLAG_ROWSTACK | CHW_FLAG_CLUSTER | CHW_FLAG_TEST_STALL)) == 0;
+      p->tier = (flags & CHW_FLAG_ROWSTACK) != 0 ? kTierRowStack : (tmem ? kTierTmem : kTierCluster);
     } else {
       p->tier = kTierFused;
     }

@@ -90,5 +90,9 @@ cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t 
 // table is generated by the build from its list of shapes, one translation unit per shape.
 FusedLaunchFn lookup_fused(int tlo, int m, int tb, int cb, int var, int om);
 
+// The tensor-memory whole-signal kernel (tmem.cuh) for m = 15, 16 in dyadic order; `units`
+// is the number of signals.  nullptr for other m.
+FusedLaunchFn lookup_tmem(int m, int var);
+
 }  // namespace chw
 

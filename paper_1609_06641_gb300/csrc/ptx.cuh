@@ -1,5 +1,6 @@
 // Thin wrappers over the sm_100+ PTX used by the CHW kernels: TMA tensor loads,
-// mbarriers, thread-block-cluster barriers and distributed shared memory (DSMEM).
+// mbarriers, thread-block-cluster barriers, distributed shared memory (DSMEM) and tensor
+// memory (tcgen05 allocation, loads and stores).
 #pragma once
 
 #include <cuda.h>
@@ -128,6 +129,85 @@ __device__ __forceinline__ uint32_t ld_dsmem_b32(uint32_t addr) {
 __device__ __forceinline__ void st_dsmem_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
                : "memory");
+}
+
+// ---------------------------------------------------------------- tensor memory (tcgen05)
+// Tensor memory is 128 lanes x 512 columns of 32-bit cells per SM.  A warp reaches only
+// the 32 lanes 32 (warp mod 4) .. +31; with the 32x32b shape thread i of the warp reads or
+// writes lane base + i, one register per column.  An address is (lane << 16) | column.
+
+// Allocate `ncols` columns (a power of two, 32..512) for this CTA; the base address is
+// written to `slot`.  One whole warp executes it.
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish_alloc_permit() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+// Free the CTA's allocation (the warp that allocated it).
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Registers v[B..B+15] to 16 consecutive columns of this thread's lane.
+template <int B, int N>
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[N]) {
+  static_assert(B >= 0 && B + 16 <= N, "register range");
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+      :
+      : "r"(taddr), "r"(v[B + 0]), "r"(v[B + 1]), "r"(v[B + 2]), "r"(v[B + 3]),
+        "r"(v[B + 4]), "r"(v[B + 5]), "r"(v[B + 6]), "r"(v[B + 7]),
+        "r"(v[B + 8]), "r"(v[B + 9]), "r"(v[B + 10]), "r"(v[B + 11]),
+        "r"(v[B + 12]), "r"(v[B + 13]), "r"(v[B + 14]), "r"(v[B + 15])
+      : "memory");
+}
+
+// Wait until this thread's earlier tensor-memory stores have completed.
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// 16 consecutive columns of this thread's lane into v[B..B+15]; the values may be used only
+// after tmem_wait_ld on the same registers.
+template <int B, int N>
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[N]) {
+  static_assert(B >= 0 && B + 16 <= N, "register range");
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      :
+        "=r"(v[B + 0]), "=r"(v[B + 1]), "=r"(v[B + 2]), "=r"(v[B + 3]),
+        "=r"(v[B + 4]), "=r"(v[B + 5]), "=r"(v[B + 6]), "=r"(v[B + 7]),
+        "=r"(v[B + 8]), "=r"(v[B + 9]), "=r"(v[B + 10]), "=r"(v[B + 11]),
+        "=r"(v[B + 12]), "=r"(v[B + 13]), "=r"(v[B + 14]), "=r"(v[B + 15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Wait until this thread's earlier tensor-memory loads have completed.  The registers
+// v[B..B+15] pass through the instruction, so no use of them is scheduled before it.
+template <int B, int N>
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[N]) {
+  static_assert(B >= 0 && B + 16 <= N, "register range");
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+      :
+        "+r"(v[B + 0]), "+r"(v[B + 1]), "+r"(v[B + 2]), "+r"(v[B + 3]),
+        "+r"(v[B + 4]), "+r"(v[B + 5]), "+r"(v[B + 6]), "+r"(v[B + 7]),
+        "+r"(v[B + 8]), "+r"(v[B + 9]), "+r"(v[B + 10]), "+r"(v[B + 11]),
+        "+r"(v[B + 12]), "+r"(v[B + 13]), "+r"(v[B + 14]), "+r"(v[B + 15])
+      :
+      : "memory");
 }
 
 // ---------------------------------------------------------------- global stores

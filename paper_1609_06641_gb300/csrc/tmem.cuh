@@ -1,0 +1,258 @@
+// Whole-signal kernel for signals of 2^15 and 2^16 four-byte elements: one signal per SM
+// at a time, with the SM's tensor memory holding the signal between its row and its
+// column butterflies, so no element leaves the SM before it is final.
+//
+// A signal of 2^M elements is R = 2^(M-14) rows of 2^14 (label bits 0..13 within a row,
+// bits 14..M-1 the row index).  Each row goes through the first three register phases of
+// the fused 2^14 tile (TMA load into shared memory, phases 1-3: label bits 0..13, in
+// order, exactly as fused.cuh runs them).  Phase 3 leaves every thread with 64 values that
+// share its thread label bits 0..7 and differ in the register label bits 8..13.  The
+// thread stores them into its own tensor-memory lane (32x32b shape: warp w reaches lanes
+// 32 (w mod 4) .. +31, and warps w and w + 4 use the two halves of the columns), 64
+// columns per row.  After the R rows the same thread reads them back: for each of its 64
+// register labels it holds the R values that differ only in the row bits, and runs the
+// cascade's last butterflies (bits 14..M-1) in registers, with no exchange between
+// threads or SMs.  Results are staged in shared memory in dyadic output order, one
+// 2^14-value chunk at a time, and written with coalesced 16-byte stores.
+//
+// Tensor memory is 128 lanes x 512 columns x 4 bytes = 256 KB per SM: one 2^16-word
+// signal.  Shared memory holds two 64 KB row buffers (the next rows' TMA loads overlap
+// the current row and the column butterflies) and a 64 KB staging buffer, which keeps one
+// CTA on each SM; the tensor-memory allocation therefore never waits for another CTA of
+// this kernel.
+#pragma once
+
+#include "fused.cuh"
+
+namespace chw {
+
+constexpr int kTmemTB = 14;  // row bits
+constexpr int kTmemThreads = 1 << (kTmemTB - 6);
+
+constexpr uint32_t bitrev_bits(uint32_t x, int n) {
+  uint32_t r = 0;
+  for (int i = 0; i < n; ++i) r |= ((x >> i) & 1u) << (n - 1 - i);
+  return r;
+}
+
+// Phase 3 of the 2^14 row tile keeps label bits 0..7 in its lanes and warps and bits 8..13
+// in its registers (the output mapping below depends on it).
+constexpr bool tmem_p3_split(const Phase& p) {
+  for (int i = 0; i < p.nreg; ++i)
+    if (p.reg[i] < 8 || p.reg[i] > 13) return false;
+  for (int i = 0; i < 5; ++i)
+    if (p.lane[i] > 7) return false;
+  for (int i = 0; i < p.nwarp; ++i)
+    if (p.warp[i] > 7) return false;
+  return p.nreg == 6 && p.ncta == 0;
+}
+
+// The staging key (bits 3..5 of a thread's output run, see below) differs between the
+// eight lanes of every quarter warp: the 16-byte staging stores are conflict-free.
+constexpr bool tmem_stage_key_ok(const Phase& p) {
+  for (int q = 0; q < 4; ++q) {
+    int seen = 0;
+    for (int ln = 8 * q; ln < 8 * q + 8; ++ln) seen |= 1 << ((bitrev_bits(lane_label(p, ln), 8) >> 3) & 7u);
+    if (seen != 0xff) return false;
+  }
+  return true;
+}
+
+template <int M>
+struct TmemCfg {
+  static_assert(M == 15 || M == 16, "tensor memory holds one signal of at most 2^16 words");
+  static constexpr int TB = kTmemTB;
+  static constexpr int R = 1 << (M - TB);  // rows per signal
+  static constexpr int JW = 64 / R;        // registers per row in one output chunk
+  static constexpr uint32_t NCOLS = 128u * R;  // two column halves of 64 R
+  static constexpr FusedPlan F = FusedCfg<0, TB, TB, 0, 0>::plan;
+  static_assert(F.has_p3 && tmem_p3_split(F.p3), "phase 3 splits the label as bits 0..7 | 8..13");
+  static_assert(tmem_stage_key_ok(F.p3), "staging stores are conflict-free");
+
+  // Output bits the thread label does not fix: the dyadic output position of label L is
+  // bitrev_M(L); the thread's label bits 0..7 give output bits M-8..M-1 (its "run" rho,
+  // 2^(M-8) outputs apart), register k of row r gives the low M-8 bits.
+  static constexpr uint32_t out_low(int r, int k) {
+    return bitrev_bits(reg_label(F.p3, k) | (static_cast<uint32_t>(r) << TB), M);
+  }
+  // Output chunk q holds the low bits [64 q, 64 q + 64), i.e. registers [q JW, (q+1) JW) of
+  // every row; src(q, w) is the index r JW + j in the chunk's register array of low bits
+  // 64 q + w (-1 if none).
+  static constexpr int src(int q, int w) {
+    for (int r = 0; r < R; ++r)
+      for (int j = 0; j < JW; ++j)
+        if (out_low(r, q * JW + j) == static_cast<uint32_t>(64 * q + w)) return r * JW + j;
+    return -1;
+  }
+  static constexpr bool chunks_ok() {
+    for (int q = 0; q < R; ++q)
+      for (int w = 0; w < 64; ++w)
+        if (src(q, w) < 0) return false;
+    return true;
+  }
+  static_assert(chunks_ok(), "each output chunk is exactly one register range of every row");
+};
+
+template <int M>
+constexpr int tmem_smem_bytes() {
+  return (12 << kTmemTB) + 1024 + 64;  // two row buffers and the staging buffer, barriers, slot
+}
+
+template <int M, class BF, bool SCALE>
+__global__ void __launch_bounds__(kTmemThreads, 1)
+    tmem_kernel(const __grid_constant__ CUtensorMap tin, const FusedArgs args, const int64_t units) {
+  using T = TmemCfg<M>;
+  constexpr int TB = T::TB, R = T::R, JW = T::JW;
+  constexpr FusedPlan F = T::F;
+  constexpr uint32_t LMASK = (1u << TB) - 1u;
+  constexpr Phase P2 = F.p2, P3 = F.p3;
+  constexpr Lin LB = F.lin_b;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  uint32_t* bufs = reinterpret_cast<uint32_t*>(base);  // row buffers g mod 2
+  uint32_t* stage = bufs + (2u << TB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (1u << TB));
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(slot, T::NCOLS);
+    tmem_relinquish_alloc_permit();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tmem = *slot;
+  // this thread's lane; row r of its values at columns (warp / 4) 64 R + 64 r + k
+  const uint32_t taddr = tmem + ((32u * (warp & 3u)) << 16) + 64u * R * (warp >> 2);
+
+  const int64_t stride = gridDim.x;
+  const int64_t first = blockIdx.x;
+  const int64_t K = first < units ? (units - first + stride - 1) / stride : 0;
+  const int64_t G = K * R;  // rows this CTA loads
+  auto elem0 = [&](int64_t k) { return unit_elem<M>(args, args.in_off, first + k * stride); };
+  auto row0 = [&](int64_t g) { return static_cast<int>((elem0(g / R) >> 5) + (g % R) * (1 << (TB - 5))); };
+  if (tid == 0) {
+    if (G > 0) tile_issue<TB>(&tin, row0(0), bufs, bar);
+    if (G > 1) tile_issue<TB>(&tin, row0(1), bufs + (1u << TB), bar + 1);
+  }
+  BF bf{};
+  if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
+  // A wait that gives up records CHW_ERR_TIMEOUT and turns this thread's later waits off.
+  bool waiting = true;
+  const uint32_t tries = args.wait_tries != 0 ? args.wait_tries : kWaitTries;
+  // output run of this thread (output bits M-8..M-1) and its staging swizzle
+  const uint32_t rho = bitrev_bits(thread_label<P3>(lane, warp, 0), 8);
+  const uint32_t sxor = ((rho >> 3) & 7u) << 2;
+  uint32_t* out = static_cast<uint32_t*>(args.out);
+
+  for (int64_t k = 0; k < K; ++k) {
+    // ---- rows: label bits 0..13, then into tensor memory
+    for (int r = 0; r < R; ++r) {
+      const int64_t g = k * R + r;
+      uint32_t* buf = bufs + ((g & 1) << TB);
+      if (waiting && !mbar_wait_bounded(bar + (g & 1), static_cast<uint32_t>((g >> 1) & 1), tries)) {
+        waiting = false;
+        if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+      }
+      uint32_t v[64];
+      phases_1_2<0, TB, TB, 0, BF>(v, elem0(k) + (int64_t{r} << TB), args, buf, bf);
+      if constexpr (!F.b_is_s) __syncthreads();
+      store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
+      __syncthreads();
+      load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, 0));
+      butterflies<P3, 11, TB>(v, bf);
+      __syncthreads();  // the row buffer is no longer read: refill it
+      if (tid == 0 && g + 2 < G) tile_issue<TB>(&tin, row0(g + 2), buf, bar + (g & 1));
+      const uint32_t col = taddr + 64u * static_cast<uint32_t>(r);
+      tmem_st16<0>(col, v);
+      tmem_st16<16>(col + 16, v);
+      tmem_st16<32>(col + 32, v);
+      tmem_st16<48>(col + 48, v);
+      tmem_wait_st();
+    }
+    // ---- label bits 14..M-1: per output chunk q, the thread's registers [q JW, (q+1) JW)
+    // of every row
+    const int64_t ob = unit_elem<M>(args, args.out_off, first + k * stride);
+    sfor<R>([&](auto qq) {
+      constexpr int q = qq;
+      uint32_t u[64];  // u[r JW + j] = row r, register q JW + j
+      sfor<R>([&](auto rr) {
+        constexpr int r = rr;
+        sfor<JW / 16>([&](auto jj) {
+          constexpr int j = 16 * jj;
+          tmem_ld16<r * JW + j>(taddr + 64u * r + q * JW + j, u);
+        });
+      });
+      tmem_wait_ld<0>(u);
+      tmem_wait_ld<16>(u);
+      tmem_wait_ld<32>(u);
+      tmem_wait_ld<48>(u);
+      sfor<M - TB>([&](auto bb) {  // label bit TB + b pairs rows r and r + 2^b
+        constexpr int b = bb;
+        sfor<R>([&](auto rr) {
+          constexpr int r = rr;
+          if constexpr (((r >> b) & 1) == 0) {
+            sfor<JW>([&](auto j) { bf(u[r * JW + j], u[(r | (1 << b)) * JW + j]); });
+          }
+        });
+      });
+      if constexpr (SCALE) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) u[i] = __float_as_uint(__fmul_rn(__uint_as_float(u[i]), args.end_scale));
+      }
+      // staged position of output low bits 64 q + w in run rho: 64 rho + w, 16-byte chunk
+      // index XOR rho's bits 3..5
+      sfor<16>([&](auto cc) {
+        constexpr int c = cc;
+        constexpr int s0 = T::src(q, 4 * c), s1 = T::src(q, 4 * c + 1);
+        constexpr int s2 = T::src(q, 4 * c + 2), s3 = T::src(q, 4 * c + 3);
+        *reinterpret_cast<uint4*>(stage + (((rho << 6) | (4u * c)) ^ sxor)) = make_uint4(u[s0], u[s1], u[s2], u[s3]);
+      });
+      __syncthreads();
+      // copy-out: 4096 chunks of 16 bytes; run i >> 4 of the chunk starts at output
+      // (i >> 4) 2^(M-8) + 64 q, so each run is 256 contiguous bytes
+#pragma unroll 4
+      for (int i = static_cast<int>(tid); i < (1 << (TB - 2)); i += kTmemThreads) {
+        const uint32_t o = static_cast<uint32_t>(i) << 2;
+        uint4 val = *reinterpret_cast<const uint4*>(stage + (o ^ (((o >> 9) & 7u) << 2)));
+        const int64_t addr = ob + (static_cast<int64_t>(o >> 6) << (M - 8)) + 64 * q + (o & 63u);
+        if (args.diag_out != nullptr) {
+          const int8_t* d = args.diag_out;
+          const int64_t di = addr & args.diag_mask;
+          if constexpr (std::is_same_v<BF, BfI32>) {
+            if (d[di] < 0) val.x = 0u - val.x;
+            if (d[di + 1] < 0) val.y = 0u - val.y;
+            if (d[di + 2] < 0) val.z = 0u - val.z;
+            if (d[di + 3] < 0) val.w = 0u - val.w;
+          } else {
+            if (d[di] < 0) val.x ^= 0x80000000u;
+            if (d[di + 1] < 0) val.y ^= 0x80000000u;
+            if (d[di + 2] < 0) val.z ^= 0x80000000u;
+            if (d[di + 3] < 0) val.w ^= 0x80000000u;
+          }
+        }
+        st_global_v4(out + addr, val.x, val.y, val.z, val.w);
+      }
+      __syncthreads();  // the staging buffer is free again
+    });
+  }
+  // Leave no TMA load in flight into shared memory, even when a wait above gave up: wait
+  // (bounded) for the last load issued on each barrier.
+  if (tid == 0) {
+    for (int64_t b = 0; b < 2 && b < G; ++b) {
+      const int64_t gl = b + ((G - 1 - b) / 2) * 2;
+      mbar_wait_bounded(bar + b, static_cast<uint32_t>((gl >> 1) & 1), kWaitTries);
+    }
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(tmem, T::NCOLS);
+}
+
+}  // namespace chw

@@ -56,8 +56,42 @@ def test_f32_every_m(chw, torch, m, norm):
     batch = 3 if m >= 13 else max(3, (1 << (14 - m)) + 5)
     x = W.normal_f32(m, batch, seed=100 + m)
     info = _check_f32(chw, torch, x, m, norm)
-    if m >= 15:
-        assert info.tier == 2 and info.cluster == 1 << (m - 14)  # thread-block cluster
+    if m in (15, 16):
+        assert info.tier == 7 and info.cluster == 1  # one CTA per signal, tensor memory
+    elif m == 17:
+        assert info.tier == 2 and info.cluster == 8  # thread-block cluster
+
+
+@pytest.mark.parametrize("m", [15, 16])
+@pytest.mark.parametrize("norm", ["per_level", "end"])
+def test_cluster_tier_on_request(chw, torch, m, norm):
+    x = W.normal_f32(m, 5, seed=140 + m)
+    info = _check_f32(chw, torch, x, m, norm, flags=chw.CHW_FLAG_CLUSTER)
+    assert info.tier == 2 and info.cluster == 1 << (m - 14)
+
+
+@pytest.mark.parametrize("m", [15, 16])
+@pytest.mark.parametrize("batch", [1, 2, 157, 331])
+def test_tmem_tier_batches(chw, torch, m, batch):
+    # 157 and 331 signals: more signals than SMs, so CTAs walk several signals and the
+    # last round leaves SMs idle; batch 1 and 2 leave most CTAs without work
+    x = W.normal_f32(m, batch, seed=170 + m + batch)
+    rows = sorted(set(np.random.default_rng(batch).choice(batch, min(batch, 6), replace=False)) | {0, batch - 1})
+    got, info = run_forward(chw, torch, x, m, "f32", "end")
+    assert info.tier == 7
+    assert_bitwise(got[rows], O.chw_cascade(x[rows], m, np.float32, "end"), f"m={m} batch={batch}")
+
+
+@pytest.mark.parametrize("m", [15, 16])
+def test_tmem_tier_norm_none_and_i32_wrap(chw, torch, m):
+    x = W.normal_f32(m, 3, seed=180 + m)
+    info = _check_f32(chw, torch, x, m, "none")
+    assert info.tier == 7
+    rng = np.random.default_rng(m)
+    xi = rng.integers(-(2**31), 2**31 - 1, size=(3, 1 << m), endpoint=True, dtype=np.int64).astype(np.int32)
+    got, info = run_forward(chw, torch, xi, m, "i32", "none")
+    assert info.tier == 7
+    assert_bitwise(got, O.chw_cascade(xi, m, np.int32, "none"), "int32 wrap")
 
 
 @pytest.mark.parametrize("m", [15, 16, 17])
@@ -151,7 +185,7 @@ def test_adjoint_is_reversed_cascade(chw, torch, m):
         assert O.rel_err_per_signal(got, x.astype(np.float64) @ O.hadamard_dyadic(m)).max() <= FP32_GATE
 
 
-@pytest.mark.parametrize("m", [6, 12, 14, 16, 19])
+@pytest.mark.parametrize("m", [6, 12, 14, 15, 16, 19])
 def test_diag_forward_and_adjoint(chw, torch, m):
     x = W.normal_f32(m, 4, seed=800 + m)
     d = W.diag_pm1(m, seed=6)
@@ -211,7 +245,7 @@ def test_config_m16_batch4096_f32_sampled(chw, torch, norm):
     m, batch = 16, 4096
     x = W.normal_f32(m, batch, seed=2)
     got, info = run_forward(chw, torch, x, m, "f32", norm)
-    assert info.tier == 2
+    assert info.tier == 7
     rows = np.random.default_rng(0).choice(batch, 6, replace=False)
     rows = np.concatenate([rows, [0, batch - 1]])
     assert_bitwise(got[rows], O.chw_cascade(x[rows], m, np.float32, norm), "m=16 sampled rows")
