@@ -146,6 +146,23 @@ chw_status_t make_rows_map(CUtensorMap* map, const void* ptr, int64_t total, int
   return CHW_OK;
 }
 
+// View `total` 4-byte words at `ptr` as rows of 2^run_bits words; boxes of 32 words x 256
+// rows, SWIZZLE_128B (the tensor-memory kernel's output stores).
+chw_status_t make_runs_map(CUtensorMap* map, const void* ptr, int64_t total, int run_bits) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (total % (int64_t{256} << run_bits) != 0) return fail(CHW_ERR_INVALID_ARG, "internal: output runs");
+  cuuint64_t dims[2] = {cuuint64_t{1} << run_bits, static_cast<cuuint64_t>(total >> run_bits)};
+  cuuint64_t strides[1] = {cuuint64_t{4} << run_bits};
+  cuuint32_t box[2] = {32, 256};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return CHW_OK;
+}
+
 }  // namespace
 
 namespace chw {
@@ -248,10 +265,12 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
 // Tensor-memory tier (m = 15, 16, dyadic order): one signal per SM at a time.
 chw_status_t launch_tmem_pass(chw_plan_s* p, const void* in, void* out, int64_t total, const int8_t* diag_in,
                               const int8_t* diag_out, cudaStream_t st) {
-  chw::FusedLaunchFn fn = chw::lookup_tmem(p->m, fused_variant(p, true));
+  chw::TmemLaunchFn fn = chw::lookup_tmem(p->m, fused_variant(p, true));
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no tensor-memory kernel for m=%d", p->m);
-  CUtensorMap map;
+  CUtensorMap map, omap;
   chw_status_t r = make_rows_map(&map, in, total, 14);
+  if (r != CHW_OK) return r;
+  r = make_runs_map(&omap, out, total, p->m - 8);
   if (r != CHW_OK) return r;
   chw::FusedArgs a{};
   a.out = out;
@@ -261,7 +280,7 @@ chw_status_t launch_tmem_pass(chw_plan_s* p, const void* in, void* out, int64_t 
   a.diag_out = diag_out;
   a.diag_mask = (int64_t{1} << p->m) - 1;
   a.status = p->d_status;
-  CHW_CUDA(fn(&map, a, total >> p->m, st));
+  CHW_CUDA(fn(&map, &omap, a, total >> p->m, st));
   return CHW_OK;
 }
 

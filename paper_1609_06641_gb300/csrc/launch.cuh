@@ -90,9 +90,13 @@ cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t 
 // table is generated by the build from its list of shapes, one translation unit per shape.
 FusedLaunchFn lookup_fused(int tlo, int m, int tb, int cb, int var, int om);
 
-// The tensor-memory whole-signal kernel (tmem.cuh) for m = 15, 16 in dyadic order; `units`
-// is the number of signals.  nullptr for other m.
-FusedLaunchFn lookup_tmem(int m, int var);
+// The tensor-memory whole-signal kernel (tmem.cuh) for m = 15, 16 in dyadic order: `tin`
+// maps the input as rows of 32 words (boxes of 256 rows), `tout` the output as rows of
+// 2^(m-8) words (boxes of 32 words x 256 rows), both SWIZZLE_128B; `units` is the number of
+// signals.  nullptr for other m.
+using TmemLaunchFn = cudaError_t (*)(const CUtensorMap* tin, const CUtensorMap* tout, const FusedArgs& args,
+                                     int64_t units, cudaStream_t st);
+TmemLaunchFn lookup_tmem(int m, int var);
 
 }  // namespace chw
 

@@ -8,7 +8,8 @@ namespace chw {
 namespace {
 
 template <int M, class BF, bool SC>
-cudaError_t launch_tmem(const CUtensorMap* tin, const FusedArgs& args, int64_t units, cudaStream_t st) {
+cudaError_t launch_tmem(const CUtensorMap* tin, const CUtensorMap* tout, const FusedArgs& args, int64_t units,
+                        cudaStream_t st) {
   constexpr auto kern = tmem_kernel<M, BF, SC>;
   constexpr int smem = tmem_smem_bytes<M>();
   static_assert(2 * smem > 233472, "one CTA per SM: the tensor-memory allocation never waits on a peer");
@@ -19,12 +20,12 @@ cudaError_t launch_tmem(const CUtensorMap* tin, const FusedArgs& args, int64_t u
   int64_t cap = persistent_cap_override();
   if (cap <= 0) cap = resident;
   if (cap > 0 && grid > cap) grid = cap;
-  kern<<<static_cast<unsigned>(grid), kTmemThreads, smem, st>>>(*tin, args, units);
+  kern<<<static_cast<unsigned>(grid), kTmemThreads, smem, st>>>(*tin, *tout, args, units);
   return cudaGetLastError();
 }
 
 template <int M>
-FusedLaunchFn tmem_variant(int var) {
+TmemLaunchFn tmem_variant(int var) {
   switch (var) {
     case kVarPerLevel: return &launch_tmem<M, BfF32PerLevel, false>;
     case kVarEnd: return &launch_tmem<M, BfF32Plain, true>;
@@ -36,7 +37,7 @@ FusedLaunchFn tmem_variant(int var) {
 
 }  // namespace
 
-FusedLaunchFn lookup_tmem(int m, int var) {
+TmemLaunchFn lookup_tmem(int m, int var) {
   if (m == 15) return tmem_variant<15>(var);
   if (m == 16) return tmem_variant<16>(var);
   return nullptr;

@@ -13,7 +13,8 @@
 // register labels it holds the R values that differ only in the row bits, and runs the
 // cascade's last butterflies (bits 14..M-1) in registers, with no exchange between
 // threads or SMs.  Results are staged in shared memory in dyadic output order, one
-// 2^14-value chunk at a time, and written with coalesced 16-byte stores.
+// 2^14-value chunk at a time, and written by TMA tensor stores that drain while the SM
+// transforms the next row.
 //
 // Tensor memory is 128 lanes x 512 columns x 4 bytes = 256 KB per SM: one 2^16-word
 // signal.  Shared memory holds two 64 KB row buffers (the next rows' TMA loads overlap
@@ -35,8 +36,24 @@ constexpr uint32_t bitrev_bits(uint32_t x, int n) {
   return r;
 }
 
-// Phase 3 of the 2^14 row tile keeps label bits 0..7 in its lanes and warps and bits 8..13
-// in its registers (the output mapping below depends on it).
+// Phase 3 of the row (label bits 11..13) with the registers on label bits 8..13 and the
+// threads on bits 0..7; lane bits 0..2 carry label bits 7, 6, 5, which are the low bits of
+// the thread's output run (the staging swizzle key, below).
+constexpr Phase make_p3_tmem() {
+  Phase p{};
+  const int r[6] = {13, 12, 11, 10, 9, 8};
+  const int l[5] = {7, 6, 5, 1, 0};
+  const int w[3] = {2, 3, 4};
+  p.nreg = 6;
+  for (int i = 0; i < 6; ++i) p.reg[i] = r[i];
+  for (int i = 0; i < 5; ++i) p.lane[i] = l[i];
+  p.nwarp = 3;
+  for (int i = 0; i < 3; ++i) p.warp[i] = w[i];
+  return p;
+}
+
+// The thread label bits 0..7 and register bits 8..13 of phase 3 (the output mapping below
+// depends on it).
 constexpr bool tmem_p3_split(const Phase& p) {
   for (int i = 0; i < p.nreg; ++i)
     if (p.reg[i] < 8 || p.reg[i] > 13) return false;
@@ -47,12 +64,12 @@ constexpr bool tmem_p3_split(const Phase& p) {
   return p.nreg == 6 && p.ncta == 0;
 }
 
-// The staging key (bits 3..5 of a thread's output run, see below) differs between the
+// The staging key (bits 0..2 of a thread's output run, see below) differs between the
 // eight lanes of every quarter warp: the 16-byte staging stores are conflict-free.
 constexpr bool tmem_stage_key_ok(const Phase& p) {
   for (int q = 0; q < 4; ++q) {
     int seen = 0;
-    for (int ln = 8 * q; ln < 8 * q + 8; ++ln) seen |= 1 << ((bitrev_bits(lane_label(p, ln), 8) >> 3) & 7u);
+    for (int ln = 8 * q; ln < 8 * q + 8; ++ln) seen |= 1 << (bitrev_bits(lane_label(p, ln), 8) & 7u);
     if (seen != 0xff) return false;
   }
   return true;
@@ -64,16 +81,23 @@ struct TmemCfg {
   static constexpr int TB = kTmemTB;
   static constexpr int R = 1 << (M - TB);  // rows per signal
   static constexpr int JW = 64 / R;        // registers per row in one output chunk
-  static constexpr uint32_t NCOLS = 128u * R;  // two column halves of 64 R
+  static constexpr uint32_t NCOLS = 512;    // two column halves: two signals of 2^15 or one of 2^16
+  // phases 1 and 2 of the fused 2^14 row tile; phase 3 and the exchange layout of our own
   static constexpr FusedPlan F = FusedCfg<0, TB, TB, 0, 0>::plan;
-  static_assert(F.has_p3 && tmem_p3_split(F.p3), "phase 3 splits the label as bits 0..7 | 8..13");
-  static_assert(tmem_stage_key_ok(F.p3), "staging stores are conflict-free");
+  static constexpr Phase P2 = F.p2;
+  static constexpr Phase P3 = make_p3_tmem();
+  static constexpr Lin LB = make_lin_b(P2, P3);
+  static constexpr bool b_is_s = lin_equal(LB, F.lin_s);
+  static_assert(F.has_p3 && phase_covers(P3, TB) && tmem_p3_split(P3), "phase 3 splits the label as 0..7 | 8..13");
+  static_assert(conflict_degree(P2, LB, (1u << TB) - 1u, false) == 1, "phase 2 writes are conflict-free");
+  static_assert(conflict_degree(P3, LB, (1u << TB) - 1u, false) == 1, "phase 3 reads are conflict-free");
+  static_assert(tmem_stage_key_ok(P3), "staging stores are conflict-free");
 
   // Output bits the thread label does not fix: the dyadic output position of label L is
   // bitrev_M(L); the thread's label bits 0..7 give output bits M-8..M-1 (its "run" rho,
   // 2^(M-8) outputs apart), register k of row r gives the low M-8 bits.
   static constexpr uint32_t out_low(int r, int k) {
-    return bitrev_bits(reg_label(F.p3, k) | (static_cast<uint32_t>(r) << TB), M);
+    return bitrev_bits(reg_label(P3, k) | (static_cast<uint32_t>(r) << TB), M);
   }
   // Output chunk q holds the low bits [64 q, 64 q + 64), i.e. registers [q JW, (q+1) JW) of
   // every row; src(q, w) is the index r JW + j in the chunk's register array of low bits
@@ -98,15 +122,34 @@ constexpr int tmem_smem_bytes() {
   return (12 << kTmemTB) + 1024 + 64;  // two row buffers and the staging buffer, barriers, slot
 }
 
+// Output tensor map of the kernel's TMA stores: the output as rows of 2^(M-8) words (one
+// output run), boxes of 32 words x 256 rows, SWIZZLE_128B.  The staging buffer holds one
+// chunk as two such boxes: words [0, 32) and [32, 64) of each of the 256 runs.
+
+// Tensor-memory column of register k (a multiple of 16) of row r of a signal whose
+// position in this CTA's sequence has parity `par`, within the thread's 256-column half.
+// 2^16: even signals keep row r in the 64-column block r, odd signals keep register block
+// k / 16 of every row in block k / 16 -- so the four registers blocks that the column
+// chunk q of an even signal reads are exactly where row q of the next (odd) signal goes,
+// and the other way round.  2^15: each parity has its own 128 columns.
+template <int M>
+__device__ __forceinline__ uint32_t tmem_col(uint32_t par, int r, int k) {
+  if constexpr (M == 16) {
+    return par ? 64u * (k >> 4) + 16u * r + (k & 15) : 64u * r + k;
+  } else {
+    return 128u * par + 64u * r + k;
+  }
+}
+
 template <int M, class BF, bool SCALE>
 __global__ void __launch_bounds__(kTmemThreads, 1)
-    tmem_kernel(const __grid_constant__ CUtensorMap tin, const FusedArgs args, const int64_t units) {
+    tmem_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+                const FusedArgs args, const int64_t units) {
   using T = TmemCfg<M>;
   constexpr int TB = T::TB, R = T::R, JW = T::JW;
-  constexpr FusedPlan F = T::F;
   constexpr uint32_t LMASK = (1u << TB) - 1u;
-  constexpr Phase P2 = F.p2, P3 = F.p3;
-  constexpr Lin LB = F.lin_b;
+  constexpr Phase P2 = T::P2, P3 = T::P3;
+  constexpr Lin LB = T::LB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   uint32_t* bufs = reinterpret_cast<uint32_t*>(base);  // row buffers g mod 2
@@ -127,8 +170,8 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tmem = *slot;
-  // this thread's lane; row r of its values at columns (warp / 4) 64 R + 64 r + k
-  const uint32_t taddr = tmem + ((32u * (warp & 3u)) << 16) + 64u * R * (warp >> 2);
+  // this thread's lane and its warp's half of the columns
+  const uint32_t taddr = tmem + ((32u * (warp & 3u)) << 16) + (T::NCOLS / 2) * (warp >> 2);
 
   const int64_t stride = gridDim.x;
   const int64_t first = blockIdx.x;
@@ -147,99 +190,107 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   const uint32_t tries = args.wait_tries != 0 ? args.wait_tries : kWaitTries;
   // output run of this thread (output bits M-8..M-1) and its staging swizzle
   const uint32_t rho = bitrev_bits(thread_label<P3>(lane, warp, 0), 8);
-  const uint32_t sxor = ((rho >> 3) & 7u) << 2;
-  uint32_t* out = static_cast<uint32_t*>(args.out);
+  const uint32_t sxor = (rho & 7u) << 2;
 
-  for (int64_t k = 0; k < K; ++k) {
-    // ---- rows: label bits 0..13, then into tensor memory
-    for (int r = 0; r < R; ++r) {
-      const int64_t g = k * R + r;
-      uint32_t* buf = bufs + ((g & 1) << TB);
-      if (waiting && !mbar_wait_bounded(bar + (g & 1), static_cast<uint32_t>((g >> 1) & 1), tries)) {
-        waiting = false;
-        if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
-      }
-      uint32_t v[64];
-      phases_1_2<0, TB, TB, 0, BF>(v, elem0(k) + (int64_t{r} << TB), args, buf, bf);
-      if constexpr (!F.b_is_s) __syncthreads();
-      store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
-      __syncthreads();
-      load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, 0));
-      butterflies<P3, 11, TB>(v, bf);
-      __syncthreads();  // the row buffer is no longer read: refill it
-      if (tid == 0 && g + 2 < G) tile_issue<TB>(&tin, row0(g + 2), buf, bar + (g & 1));
-      const uint32_t col = taddr + 64u * static_cast<uint32_t>(r);
-      tmem_st16<0>(col, v);
-      tmem_st16<16>(col + 16, v);
-      tmem_st16<32>(col + 32, v);
-      tmem_st16<48>(col + 48, v);
-      tmem_wait_st();
+  // Row r of signal k: label bits 0..13, then into tensor memory.
+  auto row = [&](int64_t k, int r) {
+    const int64_t g = k * R + r;
+    uint32_t* buf = bufs + ((g & 1) << TB);
+    if (waiting && !mbar_wait_bounded(bar + (g & 1), static_cast<uint32_t>((g >> 1) & 1), tries)) {
+      waiting = false;
+      if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
     }
-    // ---- label bits 14..M-1: per output chunk q, the thread's registers [q JW, (q+1) JW)
-    // of every row
-    const int64_t ob = unit_elem<M>(args, args.out_off, first + k * stride);
-    sfor<R>([&](auto qq) {
-      constexpr int q = qq;
-      uint32_t u[64];  // u[r JW + j] = row r, register q JW + j
+    uint32_t v[64];
+    phases_1_2<0, TB, TB, 0, BF>(v, elem0(k) + (int64_t{r} << TB), args, buf, bf);
+    if constexpr (!T::b_is_s) __syncthreads();
+    store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
+    __syncthreads();
+    load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, 0));
+    butterflies<P3, 11, TB>(v, bf);
+    __syncthreads();  // the row buffer is no longer read: refill it
+    if (tid == 0 && g + 2 < G) tile_issue<TB>(&tin, row0(g + 2), buf, bar + (g & 1));
+    const uint32_t par = static_cast<uint32_t>(k & 1);
+    tmem_st16<0>(taddr + tmem_col<M>(par, r, 0), v);
+    tmem_st16<16>(taddr + tmem_col<M>(par, r, 16), v);
+    tmem_st16<32>(taddr + tmem_col<M>(par, r, 32), v);
+    tmem_st16<48>(taddr + tmem_col<M>(par, r, 48), v);
+    tmem_wait_st();
+  };
+
+  // Output chunk q of signal k: label bits 14..M-1 on registers [q JW, (q+1) JW) of every
+  // row, staged in output order and stored by TMA.
+  auto chunk = [&](int64_t k, auto qq) {
+    constexpr int q = qq;
+    const uint32_t par = static_cast<uint32_t>(k & 1);
+    uint32_t u[64];  // u[r JW + j] = row r, register q JW + j
+    sfor<R>([&](auto rr) {
+      constexpr int r = rr;
+      sfor<JW / 16>([&](auto jj) {
+        constexpr int j = 16 * jj;
+        tmem_ld16<r * JW + j>(taddr + tmem_col<M>(par, r, q * JW + j), u);
+      });
+    });
+    tmem_wait_ld<0>(u);
+    tmem_wait_ld<16>(u);
+    tmem_wait_ld<32>(u);
+    tmem_wait_ld<48>(u);
+    sfor<M - TB>([&](auto bb) {  // label bit TB + b pairs rows r and r + 2^b
+      constexpr int b = bb;
       sfor<R>([&](auto rr) {
         constexpr int r = rr;
-        sfor<JW / 16>([&](auto jj) {
-          constexpr int j = 16 * jj;
-          tmem_ld16<r * JW + j>(taddr + 64u * r + q * JW + j, u);
-        });
-      });
-      tmem_wait_ld<0>(u);
-      tmem_wait_ld<16>(u);
-      tmem_wait_ld<32>(u);
-      tmem_wait_ld<48>(u);
-      sfor<M - TB>([&](auto bb) {  // label bit TB + b pairs rows r and r + 2^b
-        constexpr int b = bb;
-        sfor<R>([&](auto rr) {
-          constexpr int r = rr;
-          if constexpr (((r >> b) & 1) == 0) {
-            sfor<JW>([&](auto j) { bf(u[r * JW + j], u[(r | (1 << b)) * JW + j]); });
-          }
-        });
-      });
-      if constexpr (SCALE) {
-#pragma unroll
-        for (int i = 0; i < 64; ++i) u[i] = __float_as_uint(__fmul_rn(__uint_as_float(u[i]), args.end_scale));
-      }
-      // staged position of output low bits 64 q + w in run rho: 64 rho + w, 16-byte chunk
-      // index XOR rho's bits 3..5
-      sfor<16>([&](auto cc) {
-        constexpr int c = cc;
-        constexpr int s0 = T::src(q, 4 * c), s1 = T::src(q, 4 * c + 1);
-        constexpr int s2 = T::src(q, 4 * c + 2), s3 = T::src(q, 4 * c + 3);
-        *reinterpret_cast<uint4*>(stage + (((rho << 6) | (4u * c)) ^ sxor)) = make_uint4(u[s0], u[s1], u[s2], u[s3]);
-      });
-      __syncthreads();
-      // copy-out: 4096 chunks of 16 bytes; run i >> 4 of the chunk starts at output
-      // (i >> 4) 2^(M-8) + 64 q, so each run is 256 contiguous bytes
-#pragma unroll 4
-      for (int i = static_cast<int>(tid); i < (1 << (TB - 2)); i += kTmemThreads) {
-        const uint32_t o = static_cast<uint32_t>(i) << 2;
-        uint4 val = *reinterpret_cast<const uint4*>(stage + (o ^ (((o >> 9) & 7u) << 2)));
-        const int64_t addr = ob + (static_cast<int64_t>(o >> 6) << (M - 8)) + 64 * q + (o & 63u);
-        if (args.diag_out != nullptr) {
-          const int8_t* d = args.diag_out;
-          const int64_t di = addr & args.diag_mask;
-          if constexpr (std::is_same_v<BF, BfI32>) {
-            if (d[di] < 0) val.x = 0u - val.x;
-            if (d[di + 1] < 0) val.y = 0u - val.y;
-            if (d[di + 2] < 0) val.z = 0u - val.z;
-            if (d[di + 3] < 0) val.w = 0u - val.w;
-          } else {
-            if (d[di] < 0) val.x ^= 0x80000000u;
-            if (d[di + 1] < 0) val.y ^= 0x80000000u;
-            if (d[di + 2] < 0) val.z ^= 0x80000000u;
-            if (d[di + 3] < 0) val.w ^= 0x80000000u;
-          }
+        if constexpr (((r >> b) & 1) == 0) {
+          sfor<JW>([&](auto j) { bf(u[r * JW + j], u[(r | (1 << b)) * JW + j]); });
         }
-        st_global_v4(out + addr, val.x, val.y, val.z, val.w);
-      }
-      __syncthreads();  // the staging buffer is free again
+      });
     });
+    if constexpr (SCALE) {
+#pragma unroll
+      for (int i = 0; i < 64; ++i) u[i] = __float_as_uint(__fmul_rn(__uint_as_float(u[i]), args.end_scale));
+    }
+    const int64_t ob = unit_elem<M>(args, args.out_off, first + k * stride);
+    if (args.diag_out != nullptr) {  // D acts on the stored positions
+      const int8_t* d = args.diag_out + ((static_cast<int64_t>(rho) << (M - 8)) & args.diag_mask);
+      sfor<64>([&](auto ww) {
+        constexpr int w = ww;
+        constexpr int si = T::src(q, w);
+        if (d[64 * q + w] < 0) u[si] = std::is_same_v<BF, BfI32> ? 0u - u[si] : u[si] ^ 0x80000000u;
+      });
+    }
+    // The previous chunk's TMA stores have read the staging buffer.
+    if (tid == 0) bulk_wait_read();
+    __syncthreads();
+    // Output low bits 64 q + w of run rho: box w / 32, row rho, 16-byte chunk (w mod 32) / 4
+    // XOR rho mod 8 (the TMA's 128-byte swizzle).
+    sfor<16>([&](auto cc) {
+      constexpr int c = cc;
+      constexpr int s0 = T::src(q, 4 * c), s1 = T::src(q, 4 * c + 1);
+      constexpr int s2 = T::src(q, 4 * c + 2), s3 = T::src(q, 4 * c + 3);
+      constexpr uint32_t box = (c >> 3) << (TB - 1);
+      *reinterpret_cast<uint4*>(stage + box + ((rho << 5) | ((4u * (c & 7)) ^ sxor))) =
+          make_uint4(u[s0], u[s1], u[s2], u[s3]);
+    });
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      const int y = static_cast<int>(ob >> (M - 8));
+      tma_store_2d(&tout, stage, 64 * q, y);
+      tma_store_2d(&tout, stage + (1u << (TB - 1)), 64 * q + 32, y);
+      bulk_commit_group();
+    }
+  };
+
+  // Software pipeline: output chunk i of signal t-1 frees the tensor-memory columns that
+  // row i of signal t fills, so every step reads one row and writes one chunk.
+  for (int64_t t = 0; t <= K; ++t) {
+#pragma unroll 1
+    for (int i = 0; i < R; ++i) {
+      if (t >= 1) {
+        sfor<R>([&](auto qq) {
+          if (static_cast<int>(qq) == i) chunk(t - 1, qq);
+        });
+      }
+      if (t < K) row(t, i);
+    }
   }
   // Leave no TMA load in flight into shared memory, even when a wait above gave up: wait
   // (bounded) for the last load issued on each barrier.
@@ -249,6 +300,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       mbar_wait_bounded(bar + b, static_cast<uint32_t>((gl >> 1) & 1), kWaitTries);
     }
   }
+  if (tid == 0) bulk_wait_all();  // the output stores have completed
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
