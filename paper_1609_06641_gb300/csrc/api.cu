@@ -146,15 +146,15 @@ chw_status_t make_rows_map(CUtensorMap* map, const void* ptr, int64_t total, int
   return CHW_OK;
 }
 
-// View `total` 4-byte words at `ptr` as rows of 2^run_bits words; boxes of 32 words x 256
-// rows, SWIZZLE_128B (the tensor-memory kernel's output stores).
-chw_status_t make_runs_map(CUtensorMap* map, const void* ptr, int64_t total, int run_bits) {
+// View `total` 4-byte words at `ptr` as rows of 2^run_bits words; boxes of 32 words x
+// `box_rows` rows, SWIZZLE_128B (the tensor-memory kernel's output stores).
+chw_status_t make_runs_map(CUtensorMap* map, const void* ptr, int64_t total, int run_bits, int box_rows) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-  if (total % (int64_t{256} << run_bits) != 0) return fail(CHW_ERR_INVALID_ARG, "internal: output runs");
+  if (total % (int64_t{box_rows} << run_bits) != 0) return fail(CHW_ERR_INVALID_ARG, "internal: output runs");
   cuuint64_t dims[2] = {cuuint64_t{1} << run_bits, static_cast<cuuint64_t>(total >> run_bits)};
   cuuint64_t strides[1] = {cuuint64_t{4} << run_bits};
-  cuuint32_t box[2] = {32, 256};
+  cuuint32_t box[2] = {32, static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -262,26 +262,37 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
   return CHW_OK;
 }
 
-// Tensor-memory tier (m = 15, 16, dyadic order): one signal per SM at a time.
-chw_status_t launch_tmem_pass(chw_plan_s* p, const void* in, void* out, int64_t total, const int8_t* diag_in,
-                              const int8_t* diag_out, cudaStream_t st) {
-  chw::TmemLaunchFn fn = chw::lookup_tmem(p->m, fused_variant(p, true));
-  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no tensor-memory kernel for m=%d", p->m);
+// Tensor-memory kernel (M = 15, 16, dyadic or natural order) over `units` signals of 2^M
+// words: unit u at element ubase + u * ustride of `in` and `out` (ustride 0: 2^M).
+chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
+                               int64_t units, int64_t ustride, int64_t ubase, const int8_t* diag_in,
+                               const int8_t* diag_out, float scale, cudaStream_t st) {
+  chw::TmemLaunchFn fn = chw::lookup_tmem(M, var, om);
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no tensor-memory kernel for m=%d out=%d", M, om);
   CUtensorMap map, omap;
   chw_status_t r = make_rows_map(&map, in, total, 14);
   if (r != CHW_OK) return r;
-  r = make_runs_map(&omap, out, total, p->m - 8);
+  r = om == 2 ? make_runs_map(&omap, out, total, M - 6, 64) : make_runs_map(&omap, out, total, M - 8, 256);
   if (r != CHW_OK) return r;
   chw::FusedArgs a{};
   a.out = out;
   a.out_total = total;
-  a.end_scale = end_scale_f32(p->m);
+  a.end_scale = scale;
   a.diag_in = diag_in;
   a.diag_out = diag_out;
-  a.diag_mask = (int64_t{1} << p->m) - 1;
+  a.diag_mask = (int64_t{1} << M) - 1;
   a.status = p->d_status;
-  CHW_CUDA(fn(&map, &omap, a, total >> p->m, st));
+  a.unit_stride = ustride;
+  a.unit_base = ubase;
+  CHW_CUDA(fn(&map, &omap, a, units, st));
   return CHW_OK;
+}
+
+// Tensor-memory tier: the plan's batch, one signal per SM at a time.
+chw_status_t launch_tmem_pass(chw_plan_s* p, const void* in, void* out, int64_t total, const int8_t* diag_in,
+                              const int8_t* diag_out, cudaStream_t st) {
+  return launch_tmem_units(p, p->m, final_outmode(p), fused_variant(p, true), in, out, total, total >> p->m, 0, 0,
+                           diag_in, diag_out, end_scale_f32(p->m), st);
 }
 
 chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, int om, const void* in, void* out, int64_t total,
@@ -444,7 +455,8 @@ chw_status_t check_plan_args(int m, int64_t batch, chw_dtype_t dtype, chw_norm_t
 // k = 0..m-1 at [2^k, 2^{k+1}) (H_k).  The scales below 2^14 together fill the signal's
 // first 2^min(m,14) positions and run in one single-CTA "head" launch (output mode 6);
 // scales k = 14..17 run as batched launches over strided units (one unit per signal,
-// 2^m apart, at offset 2^k); each scale k >= 18 gets a one-signal two-pass plan.  Totals
+// 2^m apart, at offset 2^k; k = 15, 16 on the tensor-memory kernel, 14 and 17 on the
+// fused and cluster kernels); each scale k >= 18 gets a one-signal two-pass plan.  Totals
 // that are not whole 32-word rows (m < 5) take a ragged task set over the same offsets.
 chw_status_t build_haar_walsh(chw_plan_s* p) {
   if (is_lowp(p->dtype)) return fail(CHW_ERR_UNSUPPORTED, "Haar-Walsh takes int32 or fp32");
@@ -525,8 +537,13 @@ chw_status_t run_haar_walsh(chw_plan_s* p, const void* z, void* y, cudaStream_t 
   }
   if (r != CHW_OK) return r;
   for (int k = 14; k < m && k <= 17; ++k) {
-    r = launch_units(p, k, 0, fused_variant(p, true), z, y, total, p->batch, n, int64_t{1} << k, end_scale_f32(k), 0,
-                     st);
+    if (k == 15 || k == 16) {
+      r = launch_tmem_units(p, k, 0, fused_variant(p, true), z, y, total, p->batch, n, int64_t{1} << k, nullptr,
+                            nullptr, end_scale_f32(k), st);
+    } else {
+      r = launch_units(p, k, 0, fused_variant(p, true), z, y, total, p->batch, n, int64_t{1} << k, end_scale_f32(k),
+                       0, st);
+    }
     if (r != CHW_OK) return r;
   }
   for (int k = 18; k < m; ++k) {
@@ -632,6 +649,9 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
       return fail(CHW_ERR_UNSUPPORTED, "bf16/fp16 storage needs m <= 13 (one CTA per signal)");
     }
     p->tier = kTierSimple;  // the simple kernel stores any order
+  } else if (nat && m >= 15 && m <= 16 && (flags & (CHW_FLAG_FORCE_SIMPLE | CHW_FLAG_FORCE_MULTIPASS |
+                                                      CHW_FLAG_CLUSTER | CHW_FLAG_TEST_STALL)) == 0) {
+    p->tier = kTierTmem;  // natural order from the tensor-memory kernel's staging
   } else if (nat && m >= 15 && (flags & CHW_FLAG_FORCE_SIMPLE) == 0) {
     // natural order: single-CTA rows, then columns written as stride-2^b runs
     if (m > 23) {

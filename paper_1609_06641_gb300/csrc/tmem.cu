@@ -1,5 +1,5 @@
 // Launchers of the tensor-memory whole-signal kernel (tmem.cuh): m = 15, 16, four-byte
-// elements, dyadic order, every butterfly variant.
+// elements, dyadic or natural order, every butterfly variant.
 #include "launch.cuh"
 #include "tmem.cuh"
 
@@ -7,11 +7,11 @@ namespace chw {
 
 namespace {
 
-template <int M, class BF, bool SC>
+template <int M, class BF, bool SC, int OM>
 cudaError_t launch_tmem(const CUtensorMap* tin, const CUtensorMap* tout, const FusedArgs& args, int64_t units,
                         cudaStream_t st) {
-  constexpr auto kern = tmem_kernel<M, BF, SC>;
-  constexpr int smem = tmem_smem_bytes<M>();
+  constexpr auto kern = tmem_kernel<M, BF, SC, OM>;
+  constexpr int smem = tmem_smem_bytes();
   static_assert(2 * smem > 233472, "one CTA per SM: the tensor-memory allocation never waits on a peer");
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (attr != cudaSuccess) return attr;
@@ -24,22 +24,23 @@ cudaError_t launch_tmem(const CUtensorMap* tin, const CUtensorMap* tout, const F
   return cudaGetLastError();
 }
 
-template <int M>
+template <int M, int OM>
 TmemLaunchFn tmem_variant(int var) {
   switch (var) {
-    case kVarPerLevel: return &launch_tmem<M, BfF32PerLevel, false>;
-    case kVarEnd: return &launch_tmem<M, BfF32Plain, true>;
-    case kVarPlain: return &launch_tmem<M, BfF32Plain, false>;
-    case kVarI32: return &launch_tmem<M, BfI32, false>;
+    case kVarPerLevel: return &launch_tmem<M, BfF32PerLevel, false, OM>;
+    case kVarEnd: return &launch_tmem<M, BfF32Plain, true, OM>;
+    case kVarPlain: return &launch_tmem<M, BfF32Plain, false, OM>;
+    case kVarI32: return &launch_tmem<M, BfI32, false, OM>;
     default: return nullptr;
   }
 }
 
 }  // namespace
 
-TmemLaunchFn lookup_tmem(int m, int var) {
-  if (m == 15) return tmem_variant<15>(var);
-  if (m == 16) return tmem_variant<16>(var);
+TmemLaunchFn lookup_tmem(int m, int var, int om) {
+  if (om != 0 && om != 2) return nullptr;
+  if (m == 15) return om == 2 ? tmem_variant<15, 2>(var) : tmem_variant<15, 0>(var);
+  if (m == 16) return om == 2 ? tmem_variant<16, 2>(var) : tmem_variant<16, 0>(var);
   return nullptr;
 }
 

@@ -75,9 +75,19 @@ constexpr bool tmem_stage_key_ok(const Phase& p) {
   return true;
 }
 
-template <int M>
+// Natural order stages whole 32-word rows per warp: the lanes of phase 3 must carry label
+// bits 0..4 (output bits 0..4), so that one scalar store per register is conflict-free.
+constexpr bool tmem_natural_lanes_ok(const Phase& p) {
+  int seen = 0;
+  for (int i = 0; i < 5; ++i) seen |= 1 << p.lane[i];
+  return seen == 0x1f;
+}
+
+// OM = 0: dyadic order; OM = 2: natural (Sylvester) order, label j stored at j.
+template <int M, int OM = 0>
 struct TmemCfg {
   static_assert(M == 15 || M == 16, "tensor memory holds one signal of at most 2^16 words");
+  static_assert(OM == 0 || OM == 2, "dyadic or natural order");
   static constexpr int TB = kTmemTB;
   static constexpr int R = 1 << (M - TB);  // rows per signal
   static constexpr int JW = 64 / R;        // registers per row in one output chunk
@@ -85,13 +95,13 @@ struct TmemCfg {
   // phases 1 and 2 of the fused 2^14 row tile; phase 3 and the exchange layout of our own
   static constexpr FusedPlan F = FusedCfg<0, TB, TB, 0, 0>::plan;
   static constexpr Phase P2 = F.p2;
-  static constexpr Phase P3 = make_p3_tmem();
+  static constexpr Phase P3 = OM == 2 ? F.p3 : make_p3_tmem();
   static constexpr Lin LB = make_lin_b(P2, P3);
   static constexpr bool b_is_s = lin_equal(LB, F.lin_s);
   static_assert(F.has_p3 && phase_covers(P3, TB) && tmem_p3_split(P3), "phase 3 splits the label as 0..7 | 8..13");
   static_assert(conflict_degree(P2, LB, (1u << TB) - 1u, false) == 1, "phase 2 writes are conflict-free");
   static_assert(conflict_degree(P3, LB, (1u << TB) - 1u, false) == 1, "phase 3 reads are conflict-free");
-  static_assert(tmem_stage_key_ok(P3), "staging stores are conflict-free");
+  static_assert(OM == 2 ? tmem_natural_lanes_ok(P3) : tmem_stage_key_ok(P3), "staging stores are conflict-free");
 
   // Output bits the thread label does not fix: the dyadic output position of label L is
   // bitrev_M(L); the thread's label bits 0..7 give output bits M-8..M-1 (its "run" rho,
@@ -114,17 +124,39 @@ struct TmemCfg {
         if (src(q, w) < 0) return false;
     return true;
   }
-  static_assert(chunks_ok(), "each output chunk is exactly one register range of every row");
+  static_assert(OM == 2 || chunks_ok(), "each output chunk is exactly one register range of every row");
+
+  // Natural order: register k of row r holds output bits 8..M-1 = its label bits 8..M-1.
+  // In output chunk q they are the row psi = bits M-6..M-1 (64 rows, 2^(M-6) words apart)
+  // and the 256-word block qo = bits 8..M-7 of that row, the same for the whole chunk.
+  static constexpr uint32_t nat_high(int r, int k) { return reg_label(P3, k) | (static_cast<uint32_t>(r) << TB); }
+  static constexpr uint32_t nat_psi(int r, int k) { return nat_high(r, k) >> (M - 6); }
+  static constexpr uint32_t nat_qo(int r, int k) { return (nat_high(r, k) >> 8) & ((1u << (M - 14)) - 1u); }
+  static constexpr bool natural_ok() {
+    for (int q = 0; q < R; ++q) {
+      int seen[64] = {};
+      for (int r = 0; r < R; ++r)
+        for (int j = 0; j < JW; ++j) {
+          if (nat_qo(r, q * JW + j) != nat_qo(0, q * JW)) return false;
+          seen[nat_psi(r, q * JW + j)]++;
+        }
+      for (int i = 0; i < 64; ++i)
+        if (seen[i] != 1) return false;
+    }
+    return true;
+  }
+  static_assert(OM == 0 || natural_ok(), "a natural-order chunk is 64 rows of one 256-word block");
 };
 
-template <int M>
 constexpr int tmem_smem_bytes() {
   return (12 << kTmemTB) + 1024 + 64;  // two row buffers and the staging buffer, barriers, slot
 }
 
-// Output tensor map of the kernel's TMA stores: the output as rows of 2^(M-8) words (one
-// output run), boxes of 32 words x 256 rows, SWIZZLE_128B.  The staging buffer holds one
-// chunk as two such boxes: words [0, 32) and [32, 64) of each of the 256 runs.
+// Output tensor map of the kernel's TMA stores, SWIZZLE_128B, boxes 32 words wide.  Dyadic
+// order: the output as rows of 2^(M-8) words (one output run), boxes of 256 rows; the
+// staging buffer holds one chunk as two boxes, words [0, 32) and [32, 64) of each of the
+// 256 runs.  Natural order: rows of 2^(M-6) words, boxes of 64 rows; a chunk is eight
+// boxes, words [32 b, 32 b + 32) of one 256-word block of each of 64 rows.
 
 // Tensor-memory column of register k (a multiple of 16) of row r of a signal whose
 // position in this CTA's sequence has parity `par`, within the thread's 256-column half.
@@ -141,11 +173,11 @@ __device__ __forceinline__ uint32_t tmem_col(uint32_t par, int r, int k) {
   }
 }
 
-template <int M, class BF, bool SCALE>
+template <int M, class BF, bool SCALE, int OM>
 __global__ void __launch_bounds__(kTmemThreads, 1)
     tmem_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                 const FusedArgs args, const int64_t units) {
-  using T = TmemCfg<M>;
+  using T = TmemCfg<M, OM>;
   constexpr int TB = T::TB, R = T::R, JW = T::JW;
   constexpr uint32_t LMASK = (1u << TB) - 1u;
   constexpr Phase P2 = T::P2, P3 = T::P3;
@@ -188,8 +220,10 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   // A wait that gives up records CHW_ERR_TIMEOUT and turns this thread's later waits off.
   bool waiting = true;
   const uint32_t tries = args.wait_tries != 0 ? args.wait_tries : kWaitTries;
-  // output run of this thread (output bits M-8..M-1) and its staging swizzle
-  const uint32_t rho = bitrev_bits(thread_label<P3>(lane, warp, 0), 8);
+  // dyadic: output run of this thread (output bits M-8..M-1) and its staging swizzle;
+  // natural: its label bits 0..7 are its output bits 0..7
+  const uint32_t tl = thread_label<P3>(lane, warp, 0);
+  const uint32_t rho = bitrev_bits(tl, 8);
   const uint32_t sxor = (rho & 7u) << 2;
 
   // Row r of signal k: label bits 0..13, then into tensor memory.
@@ -248,34 +282,63 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       for (int i = 0; i < 64; ++i) u[i] = __float_as_uint(__fmul_rn(__uint_as_float(u[i]), args.end_scale));
     }
     const int64_t ob = unit_elem<M>(args, args.out_off, first + k * stride);
-    if (args.diag_out != nullptr) {  // D acts on the stored positions
-      const int8_t* d = args.diag_out + ((static_cast<int64_t>(rho) << (M - 8)) & args.diag_mask);
-      sfor<64>([&](auto ww) {
-        constexpr int w = ww;
-        constexpr int si = T::src(q, w);
-        if (d[64 * q + w] < 0) u[si] = std::is_same_v<BF, BfI32> ? 0u - u[si] : u[si] ^ 0x80000000u;
+    if constexpr (OM == 2) {
+      constexpr uint32_t qo = T::nat_qo(0, q * JW);
+      if (args.diag_out != nullptr) {  // D acts on the stored positions
+        const int8_t* d = args.diag_out + (tl & args.diag_mask);
+        sfor<64>([&](auto ii) {
+          constexpr int r = ii / JW, j = ii % JW;
+          constexpr int64_t o = T::nat_high(r, q * JW + j);  // output bits 8..M-1
+          if (d[o & args.diag_mask] < 0) u[ii] = std::is_same_v<BF, BfI32> ? 0u - u[ii] : u[ii] ^ 0x80000000u;
+        });
+      }
+      if (tid == 0) bulk_wait_read();  // the previous chunk's TMA stores have read the buffer
+      __syncthreads();
+      // word tl mod 32 of row psi in box tl / 32, 16-byte chunk XOR psi mod 8
+      uint32_t* sb = stage + ((tl >> 5) << 11) + (tl & 3u);
+      const uint32_t xc = (tl >> 2) & 7u;
+      sfor<64>([&](auto ii) {
+        constexpr int r = ii / JW, j = ii % JW;
+        constexpr uint32_t psi = T::nat_psi(r, q * JW + j);
+        sb[(psi << 5) | ((xc ^ (psi & 7u)) << 2)] = u[ii];
       });
-    }
-    // The previous chunk's TMA stores have read the staging buffer.
-    if (tid == 0) bulk_wait_read();
-    __syncthreads();
-    // Output low bits 64 q + w of run rho: box w / 32, row rho, 16-byte chunk (w mod 32) / 4
-    // XOR rho mod 8 (the TMA's 128-byte swizzle).
-    sfor<16>([&](auto cc) {
-      constexpr int c = cc;
-      constexpr int s0 = T::src(q, 4 * c), s1 = T::src(q, 4 * c + 1);
-      constexpr int s2 = T::src(q, 4 * c + 2), s3 = T::src(q, 4 * c + 3);
-      constexpr uint32_t box = (c >> 3) << (TB - 1);
-      *reinterpret_cast<uint4*>(stage + box + ((rho << 5) | ((4u * (c & 7)) ^ sxor))) =
-          make_uint4(u[s0], u[s1], u[s2], u[s3]);
-    });
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      const int y = static_cast<int>(ob >> (M - 8));
-      tma_store_2d(&tout, stage, 64 * q, y);
-      tma_store_2d(&tout, stage + (1u << (TB - 1)), 64 * q + 32, y);
-      bulk_commit_group();
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        const int y = static_cast<int>(ob >> (M - 6));
+#pragma unroll
+        for (int b = 0; b < 8; ++b) tma_store_2d(&tout, stage + (b << 11), static_cast<int>(qo) * 256 + 32 * b, y);
+        bulk_commit_group();
+      }
+    } else {
+      if (args.diag_out != nullptr) {  // D acts on the stored positions
+        const int8_t* d = args.diag_out + ((static_cast<int64_t>(rho) << (M - 8)) & args.diag_mask);
+        sfor<64>([&](auto ww) {
+          constexpr int w = ww;
+          constexpr int si = T::src(q, w);
+          if (d[64 * q + w] < 0) u[si] = std::is_same_v<BF, BfI32> ? 0u - u[si] : u[si] ^ 0x80000000u;
+        });
+      }
+      if (tid == 0) bulk_wait_read();  // the previous chunk's TMA stores have read the buffer
+      __syncthreads();
+      // Output low bits 64 q + w of run rho: box w / 32, row rho, 16-byte chunk (w mod 32) / 4
+      // XOR rho mod 8 (the TMA's 128-byte swizzle).
+      sfor<16>([&](auto cc) {
+        constexpr int c = cc;
+        constexpr int s0 = T::src(q, 4 * c), s1 = T::src(q, 4 * c + 1);
+        constexpr int s2 = T::src(q, 4 * c + 2), s3 = T::src(q, 4 * c + 3);
+        constexpr uint32_t box = (c >> 3) << (TB - 1);
+        *reinterpret_cast<uint4*>(stage + box + ((rho << 5) | ((4u * (c & 7)) ^ sxor))) =
+            make_uint4(u[s0], u[s1], u[s2], u[s3]);
+      });
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        const int y = static_cast<int>(ob >> (M - 8));
+        tma_store_2d(&tout, stage, 64 * q, y);
+        tma_store_2d(&tout, stage + (1u << (TB - 1)), 64 * q + 32, y);
+        bulk_commit_group();
+      }
     }
   };
 

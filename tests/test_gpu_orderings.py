@@ -15,7 +15,7 @@ from paper_1609_06641_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 ORACLE_DT = {"f32": np.float32, "i32": np.int32}
-TIER = {"simple": 0, "fused": 1, "cluster": 2, "two-pass": 3}
+TIER = {"simple": 0, "fused": 1, "cluster": 2, "two-pass": 3, "tensor-memory": 7}
 
 
 @pytest.fixture(scope="module")
@@ -52,6 +52,8 @@ def _expected_tier(m, batch, order):
         return TIER["simple"]
     if m <= 14:
         return TIER["fused"]
+    if order == "natural" and m <= 16:
+        return TIER["tensor-memory"]
     if order == "natural" or m >= 18:
         return TIER["two-pass"]
     return TIER["cluster"]
@@ -72,6 +74,17 @@ def test_ordered_forward_bitwise(chw, order, m, batch, dtype, norm):
     assert info.order == (1 if order == "natural" else 2)
     assert info.tier == _expected_tier(m, batch, order), (info.tier, m, batch, order)
     assert_bitwise(y, O.wht_ordered(x, m, order, ORACLE_DT[dtype], norm), f"{order} m={m} b={batch} {dtype} {norm}")
+
+
+@pytest.mark.parametrize("m", [15, 16])
+@pytest.mark.parametrize("dtype,norm", MODES)
+def test_natural_tensor_memory_many_signals(chw, m, dtype, norm):
+    # more signals than SMs: CTAs walk several signals with alternating tensor-memory layouts
+    x = _x(m, 157, dtype, 6600 + m)
+    y, info = _run(chw, x, m, "natural", dtype, norm)
+    assert info.tier == TIER["tensor-memory"]
+    rows = [0, 1, 2, 77, 155, 156]
+    assert_bitwise(y[rows], O.wht_ordered(x[rows], m, "natural", ORACLE_DT[dtype], norm), f"natural m={m} {dtype}")
 
 
 @pytest.mark.parametrize("order", ["natural", "sequency"])
