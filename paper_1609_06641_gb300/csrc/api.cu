@@ -262,7 +262,7 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
   return CHW_OK;
 }
 
-// Tensor-memory kernel (M = 15, 16, dyadic or natural order) over `units` signals of 2^M
+// Tensor-memory kernel (M = 15, 16, any order) over `units` signals of 2^M
 // words: unit u at element ubase + u * ustride of `in` and `out` (ustride 0: 2^M).
 chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
                                int64_t units, int64_t ustride, int64_t ubase, const int8_t* diag_in,
@@ -272,6 +272,7 @@ chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void
   CUtensorMap map, omap;
   chw_status_t r = make_rows_map(&map, in, total, 14);
   if (r != CHW_OK) return r;
+  // (sequency order stores through the SM; its kernel does not read the map)
   r = om == 2 ? make_runs_map(&omap, out, total, M - 6, 64) : make_runs_map(&omap, out, total, M - 8, 256);
   if (r != CHW_OK) return r;
   chw::FusedArgs a{};
@@ -681,7 +682,7 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     if (m < 5 && p->total % 32 != 0) {
       p->tier = kTierSimple;
     } else if (m >= 15) {
-      const bool tmem = m <= 16 && p->order == 0 &&
+      const bool tmem = m <= 16 && p->order != 1 &&
                         (flags & (CHW_FLAG_ROWSTACK | CHW_FLAG_CLUSTER | CHW_FLAG_TEST_STALL)) == 0;
       p->tier = (flags & CHW_FLAG_ROWSTACK) != 0 ? kTierRowStack : (tmem ? kTierTmem : kTierCluster);
     } else {

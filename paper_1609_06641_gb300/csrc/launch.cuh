@@ -90,11 +90,12 @@ cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t 
 // table is generated by the build from its list of shapes, one translation unit per shape.
 FusedLaunchFn lookup_fused(int tlo, int m, int tb, int cb, int var, int om);
 
-// The tensor-memory whole-signal kernel (tmem.cuh) for m = 15, 16 in dyadic (om = 0) or
-// natural (om = 2) order: `tin` maps the input as rows of 32 words (boxes of 256 rows),
-// `tout` the output as rows of 2^(m-8) words with boxes of 32 words x 256 rows (dyadic) or
-// rows of 2^(m-6) words with boxes of 32 x 64 (natural), all SWIZZLE_128B; `units` is the
-// number of signals.  nullptr for other shapes.
+// The tensor-memory whole-signal kernel (tmem.cuh) for m = 15, 16 in dyadic (om = 0),
+// natural (om = 2) or sequency (om = 3) order: `tin` maps the input as rows of 32 words
+// (boxes of 256 rows), `tout` the output as rows of 2^(m-8) words with boxes of 32 words x
+// 256 rows (dyadic; unused by sequency order) or rows of 2^(m-6) words with boxes of
+// 32 x 64 (natural), all SWIZZLE_128B; `units` is the number of signals.  nullptr for
+// other shapes.
 using TmemLaunchFn = cudaError_t (*)(const CUtensorMap* tin, const CUtensorMap* tout, const FusedArgs& args,
                                      int64_t units, cudaStream_t st);
 TmemLaunchFn lookup_tmem(int m, int var, int om);

@@ -1,5 +1,5 @@
 // Launchers of the tensor-memory whole-signal kernel (tmem.cuh): m = 15, 16, four-byte
-// elements, dyadic or natural order, every butterfly variant.
+// elements, dyadic, natural or sequency order, every butterfly variant.
 #include "launch.cuh"
 #include "tmem.cuh"
 
@@ -37,10 +37,19 @@ TmemLaunchFn tmem_variant(int var) {
 
 }  // namespace
 
+template <int M>
+TmemLaunchFn tmem_order(int var, int om) {
+  switch (om) {
+    case 0: return tmem_variant<M, 0>(var);
+    case 2: return tmem_variant<M, 2>(var);
+    case 3: return tmem_variant<M, 3>(var);
+    default: return nullptr;
+  }
+}
+
 TmemLaunchFn lookup_tmem(int m, int var, int om) {
-  if (om != 0 && om != 2) return nullptr;
-  if (m == 15) return om == 2 ? tmem_variant<15, 2>(var) : tmem_variant<15, 0>(var);
-  if (m == 16) return om == 2 ? tmem_variant<16, 2>(var) : tmem_variant<16, 0>(var);
+  if (m == 15) return tmem_order<15>(var, om);
+  if (m == 16) return tmem_order<16>(var, om);
   return nullptr;
 }
 

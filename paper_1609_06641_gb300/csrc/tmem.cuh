@@ -83,11 +83,12 @@ constexpr bool tmem_natural_lanes_ok(const Phase& p) {
   return seen == 0x1f;
 }
 
-// OM = 0: dyadic order; OM = 2: natural (Sylvester) order, label j stored at j.
+// OM = 0: dyadic order; OM = 2: natural (Sylvester) order, label j stored at j; OM = 3:
+// sequency (Walsh) order, dyadic position p stored at gray^{-1}(p).
 template <int M, int OM = 0>
 struct TmemCfg {
   static_assert(M == 15 || M == 16, "tensor memory holds one signal of at most 2^16 words");
-  static_assert(OM == 0 || OM == 2, "dyadic or natural order");
+  static_assert(OM == 0 || OM == 2 || OM == 3, "dyadic, natural or sequency order");
   static constexpr int TB = kTmemTB;
   static constexpr int R = 1 << (M - TB);  // rows per signal
   static constexpr int JW = 64 / R;        // registers per row in one output chunk
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
         bulk_commit_group();
       }
     } else {
-      if (args.diag_out != nullptr) {  // D acts on the stored positions
+      if (OM == 0 && args.diag_out != nullptr) {  // D acts on the stored positions
         const int8_t* d = args.diag_out + ((static_cast<int64_t>(rho) << (M - 8)) & args.diag_mask);
         sfor<64>([&](auto ww) {
           constexpr int w = ww;
@@ -331,13 +332,53 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
         *reinterpret_cast<uint4*>(stage + box + ((rho << 5) | ((4u * (c & 7)) ^ sxor))) =
             make_uint4(u[s0], u[s1], u[s2], u[s3]);
       });
-      fence_proxy_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        const int y = static_cast<int>(ob >> (M - 8));
-        tma_store_2d(&tout, stage, 64 * q, y);
-        tma_store_2d(&tout, stage + (1u << (TB - 1)), 64 * q + 32, y);
-        bulk_commit_group();
+      if constexpr (OM == 0) {
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          const int y = static_cast<int>(ob >> (M - 8));
+          tma_store_2d(&tout, stage, 64 * q, y);
+          tma_store_2d(&tout, stage + (1u << (TB - 1)), 64 * q + 32, y);
+          bulk_commit_group();
+        }
+      } else {
+        // Sequency order scatters the runs (gray^{-1} of their high bits), so the chunk goes
+        // out through the SM: a warp copies four 32-element aligned blocks, and gray^{-1}
+        // maps an aligned block onto an aligned block (reordered inside), so each warp store
+        // is four whole 128-byte lines.
+        __syncthreads();
+        uint32_t* out = static_cast<uint32_t*>(args.out);
+#pragma unroll 4
+        for (int i = static_cast<int>(tid); i < (1 << (TB - 2)); i += kTmemThreads) {
+          const uint32_t h = static_cast<uint32_t>(i) >> (TB - 3), run = (static_cast<uint32_t>(i) >> 3) & 255u;
+          const uint32_t c8 = static_cast<uint32_t>(i) & 7u;
+          uint4 val = *reinterpret_cast<const uint4*>(stage + (h << (TB - 1)) + (run << 5) + ((c8 ^ (run & 7u)) << 2));
+          // dyadic position / 4 within the signal, and its gray^{-1}
+          const uint32_t p4 = (run << (M - 10)) | static_cast<uint32_t>(16 * q) | (h << 3) | c8;
+          uint32_t g = p4;
+          g ^= g >> 1;
+          g ^= g >> 2;
+          g ^= g >> 4;
+          g ^= g >> 8;
+          g ^= g >> 16;
+          val = (__popc(p4) & 1) ? make_uint4(val.z, val.w, val.y, val.x) : make_uint4(val.x, val.y, val.w, val.z);
+          const int64_t addr = ob + (static_cast<int64_t>(g) << 2);
+          if (args.diag_out != nullptr) {  // D acts on the stored positions
+            const int8_t* d = args.diag_out + (addr & args.diag_mask);
+            if constexpr (std::is_same_v<BF, BfI32>) {
+              if (d[0] < 0) val.x = 0u - val.x;
+              if (d[1] < 0) val.y = 0u - val.y;
+              if (d[2] < 0) val.z = 0u - val.z;
+              if (d[3] < 0) val.w = 0u - val.w;
+            } else {
+              if (d[0] < 0) val.x ^= 0x80000000u;
+              if (d[1] < 0) val.y ^= 0x80000000u;
+              if (d[2] < 0) val.z ^= 0x80000000u;
+              if (d[3] < 0) val.w ^= 0x80000000u;
+            }
+          }
+          st_global_v4(out + addr, val.x, val.y, val.z, val.w);
+        }
       }
     }
   };

@@ -52,7 +52,7 @@ def _expected_tier(m, batch, order):
         return TIER["simple"]
     if m <= 14:
         return TIER["fused"]
-    if order == "natural" and m <= 16:
+    if m <= 16:
         return TIER["tensor-memory"]
     if order == "natural" or m >= 18:
         return TIER["two-pass"]
@@ -76,15 +76,24 @@ def test_ordered_forward_bitwise(chw, order, m, batch, dtype, norm):
     assert_bitwise(y, O.wht_ordered(x, m, order, ORACLE_DT[dtype], norm), f"{order} m={m} b={batch} {dtype} {norm}")
 
 
+@pytest.mark.parametrize("order", ["natural", "sequency"])
 @pytest.mark.parametrize("m", [15, 16])
 @pytest.mark.parametrize("dtype,norm", MODES)
-def test_natural_tensor_memory_many_signals(chw, m, dtype, norm):
+def test_ordered_tensor_memory_many_signals(chw, order, m, dtype, norm):
     # more signals than SMs: CTAs walk several signals with alternating tensor-memory layouts
     x = _x(m, 157, dtype, 6600 + m)
-    y, info = _run(chw, x, m, "natural", dtype, norm)
+    y, info = _run(chw, x, m, order, dtype, norm)
     assert info.tier == TIER["tensor-memory"]
     rows = [0, 1, 2, 77, 155, 156]
-    assert_bitwise(y[rows], O.wht_ordered(x[rows], m, "natural", ORACLE_DT[dtype], norm), f"natural m={m} {dtype}")
+    assert_bitwise(y[rows], O.wht_ordered(x[rows], m, order, ORACLE_DT[dtype], norm), f"{order} m={m} {dtype}")
+
+
+@pytest.mark.parametrize("m", [15, 16])
+def test_sequency_cluster_tier_on_request(chw, m):
+    x = _x(m, 3, "f32", 6700 + m)
+    y, info = _run(chw, x, m, "sequency", "f32", "end", flags=chw.CHW_FLAG_CLUSTER)
+    assert info.tier == TIER["cluster"]
+    assert_bitwise(y, O.wht_ordered(x, m, "sequency", np.float32, "end"), f"cluster sequency m={m}")
 
 
 @pytest.mark.parametrize("order", ["natural", "sequency"])
