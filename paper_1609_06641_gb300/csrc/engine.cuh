@@ -364,8 +364,7 @@ struct BfF32Plain {
 // (a, b) -> ((a+b) c, (a-b) c), each operation rounded to nearest even.  The packed form
 // adds and subtracts with f32x2 but multiplies with scalar mul.rn: a packed multiply feeding
 // the next level's packed add was observed to be fused into one FMA by the assembler (a
-// GB300 probe of chained levels), which would round differently from the cascade; a packed
-// FMA with a -0 addend in its place gave 1-ulp differences on GB300 as well.
+// GB300 probe of chained levels), which would round differently from the cascade.
 struct BfF32PerLevel {
   static constexpr bool kPacked = true;
   float c;
