@@ -346,6 +346,21 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
         rec(f"m{m}_b{b}_f32_two_pass", 2 * xl.numel() * 4, ms, 2,
             dram_pass_frac=round(gbs(4 * xl.numel() * 4, ms / 1e3) / peak, 4))
         del xl, yl, pl
+    # autotuned plans (the tuner times every candidate configuration when the plan is made):
+    # the built-in choice and the tuned one, side by side
+    for m, b in ((17, 2048), (20, 256), (22, 64)):
+        xa = torch.randn(b, 1 << m, device=dev, generator=g)
+        ya = torch.empty_like(xa)
+        for tag, fl in (("builtin", 0), ("autotuned", chw.CHW_FLAG_AUTOTUNE)):
+            t0 = time.perf_counter()
+            pa = chw.chw_plan(m, b, "f32", "end", fl)
+            plan_s = time.perf_counter() - t0
+            ia = chw.chw_plan_get_info(pa)
+            ms = time_device(lambda: chw.chw_forward(pa, xa, ya), k, warmup, 1, st)
+            rec(f"m{m}_b{b}_f32_{tag}", 2 * xa.numel() * 4, ms, ia.kernels_per_call, tier=int(ia.tier),
+                row_bits=int(ia.row_bits), tile_bits=int(ia.tile_bits), plan_ms=round(plan_s * 1e3, 1))
+            del pa
+        del xa, ya
     # 16-bit storage, m = 12, batch 16384
     for fmt, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
         xq = (torch.randn(16384, 1 << 12, device=dev, generator=g)).to(tdt)

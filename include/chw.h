@@ -84,6 +84,10 @@ typedef enum chw_norm_e {
                                     /* CHW_ERR_TIMEOUT; the output is then undefined       */
 #define CHW_FLAG_CLUSTER 128u       /* m = 15, 16: thread-block-cluster (DSMEM) tier instead */
                                     /* of the tensor-memory tier                           */
+#define CHW_FLAG_AUTOTUNE 256u      /* pick the tier, two-pass split and CTA tile by timing */
+                                    /* the candidates (chw_tune_candidates) on the device  */
+                                    /* when the plan is made; CHW_AUTOTUNE=1 in the        */
+                                    /* environment turns it on for every plan              */
 
 typedef struct chw_plan_s* chw_plan_t;
 
@@ -103,7 +107,17 @@ typedef struct chw_plan_info_s {
   int64_t workspace_bytes;   /* device scratch owned by the plan                       */
   int64_t total_elements;    /* elements per call (sum over the batch)                 */
   int order;                 /* output order: 0 dyadic, 1 natural, 2 sequency          */
+  int tile_bits;             /* CTA tile of the fused/cluster kernels (13, 14; 0 default) */
+  int tuned;                 /* 0 built-in choice, 1 timed by the autotuner, 2 its cache */
+  float tune_us;             /* the autotuner's time for the chosen configuration (us) */
 } chw_plan_info_t;
+
+/* One configuration the autotuner can choose for a plan. */
+typedef struct chw_tune_choice_s {
+  int tier;                  /* as chw_plan_info_t.tier                                */
+  int row_bits;              /* two-pass: bits of the first (row) pass; otherwise m     */
+  int tile_bits;             /* CTA tile of the fused/cluster kernels: 13 or 14; 0 none */
+} chw_tune_choice_t;
 
 /*
  * chw_plan -- prepare y = H_m x for `batch` signals of length 2^m (eq. (1), Theorem 1).
@@ -258,6 +272,37 @@ chw_status_t chw_forward_noalloc(int m, int64_t batch, chw_dtype_t dtype, chw_no
 
 /* Fill *info with what the plan launches. */
 chw_status_t chw_plan_get_info(chw_plan_t plan, chw_plan_info_t* info);
+
+/*
+ * Autotuner.  A plan made with CHW_FLAG_AUTOTUNE (or with CHW_AUTOTUNE=1 in the
+ * environment) times every candidate configuration of its shape on the device -- on
+ * min(batch, 2^26 / 2^m) synthetic signals, two warm-up runs and the mean of five, CUDA
+ * events -- and keeps the fastest; chw_plan_get_info reports the choice (tier, row_bits,
+ * tile_bits, tuned = 1) and its time.  Every candidate computes the same result bit for bit.
+ * Choices are cached per process under (device name, m, floor(log2 batch), dtype, norm,
+ * order); a later plan with the same key takes the cached choice (tuned = 2).  When
+ * CHW_TUNE_CACHE names a file, it is read on the first autotuned plan and rewritten after
+ * each new measurement.  Plans with a single configuration (m <= 13, bf16/fp16, or a flag
+ * that fixes the tier) are not timed.
+ *
+ * chw_tune_candidates   host only: writes up to `cap` candidates for this shape to `out`
+ *                       and returns how many there are (0: nothing to choose).
+ * chw_tune_cache_put/get host only: set / read the process cache entry of a key, the device
+ *                       named by `device` (as cudaDeviceProp.name); get returns
+ *                       CHW_ERR_UNSUPPORTED when the key has no entry.
+ * chw_tune_cache_load   merges a cache file into the process cache; returns the number of
+ *                       entries read (malformed lines are skipped) or -1 if unreadable.
+ * chw_tune_cache_save   writes the process cache to `path` (CHW_ERR_INVALID_ARG on I/O error).
+ * chw_tune_cache_clear  empties the process cache.
+ */
+int chw_tune_candidates(int m, chw_dtype_t dtype, chw_norm_t norm, uint32_t flags, chw_tune_choice_t* out, int cap);
+chw_status_t chw_tune_cache_put(const char* device, int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm,
+                                uint32_t flags, const chw_tune_choice_t* choice, float us);
+chw_status_t chw_tune_cache_get(const char* device, int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm,
+                                uint32_t flags, chw_tune_choice_t* choice, float* us);
+int chw_tune_cache_load(const char* path);
+chw_status_t chw_tune_cache_save(const char* path);
+void chw_tune_cache_clear(void);
 
 /*
  * chw_last_device_status -- synchronise the plan's device work and report the first

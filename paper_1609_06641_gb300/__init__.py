@@ -13,12 +13,14 @@ no CPU fallback; a missing library raises.
 """
 
 import ctypes
+import os
 
 from . import _lib
 from ._lib import (
     CHW_BF16,
     CHW_F16,
     CHW_F32,
+    CHW_FLAG_AUTOTUNE,
     CHW_FLAG_CLUSTER,
     CHW_FLAG_HAAR_WALSH,
     CHW_FLAG_ORDER_NATURAL,
@@ -275,6 +277,54 @@ def chw_plan_get_info(plan):
     info = _lib.chw_plan_info_t()
     _lib.check(_lib.load().chw_plan_get_info(plan.handle, ctypes.byref(info)), "chw_plan_get_info")
     return info
+
+
+def chw_tune_candidates(m, dtype="f32", norm="end", flags=CHW_FLAG_NONE, order="dyadic"):
+    """Configurations the autotuner times for this shape: a list of (tier, row_bits, tile_bits)."""
+    lib = _lib.load()
+    d = _code(dtype, DTYPES, "dtype")
+    nm = _code(norm, NORMS, "norm")
+    fl = int(flags) | _code(order, ORDERS, "order")
+    n = lib.chw_tune_candidates(int(m), d, nm, fl, None, 0)
+    arr = (_lib.chw_tune_choice_t * max(n, 1))()
+    lib.chw_tune_candidates(int(m), d, nm, fl, arr, n)
+    return [(c.tier, c.row_bits, c.tile_bits) for c in arr[:n]]
+
+
+def chw_tune_cache_put(device, m, batch, dtype, norm, choice, us, flags=CHW_FLAG_NONE, order="dyadic"):
+    """Set the autotuner's cache entry of a key; ``choice`` = (tier, row_bits, tile_bits)."""
+    c = _lib.chw_tune_choice_t(*[int(v) for v in choice])
+    fl = int(flags) | _code(order, ORDERS, "order")
+    _lib.check(
+        _lib.load().chw_tune_cache_put(device.encode(), int(m), int(batch), _code(dtype, DTYPES, "dtype"),
+                                       _code(norm, NORMS, "norm"), fl, ctypes.byref(c), float(us)),
+        "chw_tune_cache_put",
+    )
+
+
+def chw_tune_cache_get(device, m, batch, dtype, norm, flags=CHW_FLAG_NONE, order="dyadic"):
+    """The cached (tier, row_bits, tile_bits) and time of a key, or None."""
+    c = _lib.chw_tune_choice_t()
+    us = ctypes.c_float()
+    fl = int(flags) | _code(order, ORDERS, "order")
+    st = _lib.load().chw_tune_cache_get(device.encode(), int(m), int(batch), _code(dtype, DTYPES, "dtype"),
+                                        _code(norm, NORMS, "norm"), fl, ctypes.byref(c), ctypes.byref(us))
+    if st == _lib.CHW_ERR_UNSUPPORTED:
+        return None
+    _lib.check(st, "chw_tune_cache_get")
+    return (c.tier, c.row_bits, c.tile_bits), us.value
+
+
+def chw_tune_cache_load(path):
+    return _lib.load().chw_tune_cache_load(os.fsencode(path))
+
+
+def chw_tune_cache_save(path):
+    _lib.check(_lib.load().chw_tune_cache_save(os.fsencode(path)), "chw_tune_cache_save")
+
+
+def chw_tune_cache_clear():
+    _lib.load().chw_tune_cache_clear()
 
 
 def chw_last_device_status(plan):

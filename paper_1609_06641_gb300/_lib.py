@@ -36,6 +36,7 @@ CHW_FLAG_ORDER_NATURAL = 16
 CHW_FLAG_ORDER_SEQUENCY = 32
 CHW_FLAG_TEST_STALL = 64
 CHW_FLAG_CLUSTER = 128
+CHW_FLAG_AUTOTUNE = 256
 
 
 class chw_plan_info_t(ctypes.Structure):
@@ -52,7 +53,14 @@ class chw_plan_info_t(ctypes.Structure):
         ("workspace_bytes", ctypes.c_int64),
         ("total_elements", ctypes.c_int64),
         ("order", ctypes.c_int),
+        ("tile_bits", ctypes.c_int),
+        ("tuned", ctypes.c_int),
+        ("tune_us", ctypes.c_float),
     ]
+
+
+class chw_tune_choice_t(ctypes.Structure):
+    _fields_ = [("tier", ctypes.c_int), ("row_bits", ctypes.c_int), ("tile_bits", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -74,6 +82,23 @@ _SIGNATURES = {
     "chw_plan_destroy": (ctypes.c_int, [_P]),
     "chw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "chw_last_error_message": (ctypes.c_char_p, []),
+    "chw_tune_candidates": (
+        ctypes.c_int,
+        [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(chw_tune_choice_t), ctypes.c_int],
+    ),
+    "chw_tune_cache_put": (
+        ctypes.c_int,
+        [ctypes.c_char_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32,
+         ctypes.POINTER(chw_tune_choice_t), ctypes.c_float],
+    ),
+    "chw_tune_cache_get": (
+        ctypes.c_int,
+        [ctypes.c_char_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32,
+         ctypes.POINTER(chw_tune_choice_t), ctypes.POINTER(ctypes.c_float)],
+    ),
+    "chw_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "chw_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "chw_tune_cache_clear": (None, []),
 }
 
 _lib = None

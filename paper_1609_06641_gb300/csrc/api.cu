@@ -3,6 +3,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -17,6 +18,7 @@
 #include "ragged.cuh"
 #include "simple.cuh"
 #include "lowp.cuh"
+#include "tune.h"
 
 namespace chw {
 using LowpLaunchFn = cudaError_t (*)(const CUtensorMap*, const LowpArgs&, int64_t, cudaStream_t);
@@ -90,17 +92,20 @@ int two_pass_col_bits(int m) {
   return m <= 28 ? 11 : 12;
 }
 
-// One-pass row kernel shape for a transform of M bits.
-Shape row_shape(int M) {
+// One-pass row kernel shape for a transform of M bits; `tb` = preferred CTA tile bits for
+// shapes that span more than a 2^13-word tile (13 or 14; 0: the default above).
+Shape row_shape(int M, int tb = 0) {
+  if (tb == 0) tb = cluster_tile_bits();
   if (M <= 13) return {13, 0};
-  if (M <= 16 && cluster_tile_bits() == 13) return {13, M - 13};
+  if (M <= 16 && tb == 13) return {13, M - 13};
   if (M == 14) return {14, 0};
   return {14, M - 14};
 }
 // Second-pass column kernel shape for A row bits (32 columns per block).
-Shape col_shape(int A) {
+Shape col_shape(int A, int tb = 0) {
+  if (tb == 0) tb = cluster_tile_bits();
   if (A <= 8) return {13, 0};
-  if (A <= 11 && cluster_tile_bits() == 13) return {13, A - 8};
+  if (A <= 11 && tb == 13) return {13, A - 8};
   if (A == 9) return {14, 0};
   return {14, A - 9};
 }
@@ -187,6 +192,9 @@ struct chw_plan_s {
   int row_bits = 0;  // two-pass: b (pass 1 rows); a = m - b
   int64_t rowstack_slots = 0;  // row-stack tier: scratch slots of 2^m words (one per CTA)
   int order = 0;               // 0 dyadic, 1 natural, 2 sequency
+  int tile_bits = 0;           // fused / cluster CTA tile bits (0: the default)
+  int tuned = 0;               // 0 built-in choice, 1 timed by the autotuner, 2 from its cache
+  float tune_us = 0.f;         // the autotuner's time for the chosen configuration
   int64_t total = 0;
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
@@ -237,7 +245,7 @@ chw_status_t validate_data_ptr(const void* p, const char* name) {
 chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
                              const int8_t* diag_in, const int8_t* diag_out, int64_t diag_mask, int colblock_a,
                              float scale, cudaStream_t st) {
-  const Shape s = row_shape(M);
+  const Shape s = row_shape(M, p->tile_bits);
   chw::FusedLaunchFn fn = chw::lookup_fused(0, M, s.tb, s.cb, var, om);
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no row kernel for M=%d tb=%d cb=%d out=%d", M, s.tb, s.cb, om);
   CUtensorMap map;
@@ -298,7 +306,7 @@ chw_status_t launch_tmem_pass(chw_plan_s* p, const void* in, void* out, int64_t 
 
 chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, int om, const void* in, void* out, int64_t total,
                              const int8_t* diag_out, int64_t diag_mask, float scale, cudaStream_t st) {
-  const Shape s = om == 2 ? Shape{A <= 8 ? 13 : 14, 0} : col_shape(A);
+  const Shape s = om == 2 ? Shape{A <= 8 ? 13 : 14, 0} : col_shape(A, p->tile_bits);
   chw::FusedLaunchFn fn = chw::lookup_fused(5, A, s.tb, s.cb, var, om);
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no column kernel for A=%d", A);
   CUtensorMap map;
@@ -598,6 +606,194 @@ void destroy_host_pipeline(chw_plan_s* p) {
   p->h_chunk = 0;
 }
 
+// ---------------------------------------------------------------- autotuner
+// The configurations a plan of this shape can run, every one of them compiled: for m = 14
+// the 2^14-word tile or a 2-CTA cluster of 2^13-word tiles; for m = 15, 16 the tensor-memory
+// kernel, 2- or 4-CTA clusters of 2^14- or 2^13-word tiles and the row-stack tier; for
+// m = 17 the 8-CTA cluster and the row-stack tier; for m >= 17 every two-pass split
+// y = H_b X^T H_a with a = 6..12 (b = m - a in 5..17) and either tile size.  Empty when the
+// plan has a single configuration (m <= 13, 16-bit storage, or a flag that fixes the tier).
+std::vector<chw::TuneChoice> tune_candidates(int m, chw_dtype_t dtype, chw_norm_t norm, uint32_t flags) {
+  std::vector<chw::TuneChoice> c;
+  const uint32_t fixed = CHW_FLAG_FORCE_SIMPLE | CHW_FLAG_FORCE_MULTIPASS | CHW_FLAG_ROWSTACK | CHW_FLAG_CLUSTER |
+                         CHW_FLAG_TEST_STALL;
+  if (is_lowp(dtype) || (flags & fixed) != 0 || m < 14 || m > 29) return c;
+  const int order = (flags & CHW_FLAG_ORDER_NATURAL) != 0 ? 1 : ((flags & CHW_FLAG_ORDER_SEQUENCY) != 0 ? 2 : 0);
+  const int om = m <= 1 ? 0 : (order == 1 ? 2 : (order == 2 ? 3 : 0));
+  int var_last, var_first;
+  if (dtype == CHW_I32) {
+    var_last = var_first = chw::kVarI32;
+  } else if (norm == CHW_NORM_PER_LEVEL) {
+    var_last = var_first = chw::kVarPerLevel;
+  } else {
+    var_first = chw::kVarPlain;
+    var_last = norm == CHW_NORM_END ? chw::kVarEnd : chw::kVarPlain;
+  }
+  auto add = [&](int tier, int row_bits, int tile_bits) {
+    for (const auto& x : c)
+      if (x.tier == tier && x.row_bits == row_bits && x.tile_bits == tile_bits) return;
+    c.push_back(chw::TuneChoice{tier, row_bits, tile_bits});
+  };
+  if (m <= 17) {
+    if (m <= 16 && chw::lookup_tmem(m, var_last, om) != nullptr) add(kTierTmem, m, 0);
+    for (int tb : {14, 13}) {
+      const Shape sh = row_shape(m, tb);
+      if (sh.tb != tb && m != 17) continue;  // the tile preference does not apply
+      if (chw::lookup_fused(0, m, sh.tb, sh.cb, var_last, om) != nullptr)
+        add(sh.cb > 0 ? kTierCluster : kTierFused, m, sh.tb);
+    }
+    if (om == 0 && m >= 15 && chw::lookup_rowstack(m, var_last) != nullptr) add(kTierRowStack, m, 14);
+  }
+  if (m >= 17) {
+    for (int a = 6; a <= 12; ++a) {
+      const int b = m - a;
+      if (b < 5 || b > 17) continue;
+      for (int tb : {14, 13}) {
+        const Shape s1 = row_shape(b, tb);
+        const Shape s2 = om == 2 ? Shape{a <= 8 ? 13 : 14, 0} : col_shape(a, tb);
+        const int om1 = om == 2 ? 4 : 1;
+        if (chw::lookup_fused(0, b, s1.tb, s1.cb, var_first, om1) == nullptr ||
+            chw::lookup_fused(5, a, s2.tb, s2.cb, var_last, om) == nullptr)
+          continue;
+        const bool same = row_shape(b, 13).tb == row_shape(b, 14).tb && row_shape(b, 13).cb == row_shape(b, 14).cb &&
+                          (om == 2 || (col_shape(a, 13).tb == col_shape(a, 14).tb && col_shape(a, 13).cb == col_shape(a, 14).cb));
+        add(kTierTwoPass, b, same ? 14 : tb);
+      }
+    }
+  }
+  if (c.size() <= 1) c.clear();
+  return c;
+}
+
+void apply_choice(chw_plan_s* p, const chw::TuneChoice& c) {
+  p->tier = c.tier;
+  p->row_bits = c.row_bits;
+  p->tile_bits = c.tile_bits;
+  p->passes = c.tier == kTierTwoPass ? 2 : 1;
+}
+
+bool autotune_requested(uint32_t flags) {
+  if ((flags & CHW_FLAG_AUTOTUNE) != 0) return true;
+  const char* e = std::getenv("CHW_AUTOTUNE");
+  return e != nullptr && std::atoi(e) != 0;
+}
+
+// The cache file named by CHW_TUNE_CACHE, read once per process.
+const char* tune_cache_path() {
+  static std::once_flag once;
+  static std::string path;
+  std::call_once(once, [] {
+    const char* e = std::getenv("CHW_TUNE_CACHE");
+    if (e != nullptr && *e != 0) {
+      path = e;
+      chw::tune_cache_load(path.c_str());
+    }
+  });
+  return path.empty() ? nullptr : path.c_str();
+}
+
+// Pick the plan's configuration by timing every candidate (CUDA events, default stream) on
+// synthetic signals of the plan's shape: min(batch, 2^26 / 2^m) signals (at least one), so
+// that a candidate's run covers more than the L2; two warm-up runs, then the mean of five.
+// A cached choice for the same key is used instead of timing (if it is still a candidate).
+chw_status_t autotune_plan(chw_plan_s* p) {
+  const std::vector<chw::TuneChoice> cands = tune_candidates(p->m, p->dtype, p->norm, p->flags);
+  if (cands.empty()) return CHW_OK;
+  cudaDeviceProp prop{};
+  CHW_CUDA(cudaGetDeviceProperties(&prop, p->device));
+  const std::string key = chw::tune_key(prop.name, p->m, p->batch, p->dtype, p->norm, p->order);
+  const char* path = tune_cache_path();
+  chw::TuneChoice hit{};
+  float hit_us = 0.f;
+  if (chw::tune_cache_get(key, &hit, &hit_us)) {
+    for (const auto& c : cands)
+      if (c.tier == hit.tier && c.row_bits == hit.row_bits && c.tile_bits == hit.tile_bits) {
+        apply_choice(p, c);
+        p->tuned = 2;
+        p->tune_us = hit_us;
+        return CHW_OK;
+      }
+  }
+  const int64_t n = int64_t{1} << p->m;
+  int64_t tbatch = (int64_t{1} << 26) / n;
+  if (tbatch < 1) tbatch = 1;
+  if (tbatch > p->batch) tbatch = p->batch;
+  const int64_t total = tbatch * n;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  const int64_t slots = std::min<int64_t>(sms > 0 ? sms : 1, tbatch);
+  const size_t bytes = static_cast<size_t>(total) * 4;
+  const size_t ws_bytes = std::max(bytes, static_cast<size_t>(slots * n) * 4);
+  void *x = nullptr, *y = nullptr, *ws = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&] {
+    if (x) cudaFree(x);
+    if (y) cudaFree(y);
+    if (ws) cudaFree(ws);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess ||
+      cudaMalloc(&ws, ws_bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    release();
+    cudaGetLastError();
+    return fail(CHW_ERR_OOM, "autotuner buffers of %zu bytes", 2 * bytes + ws_bytes);
+  }
+  cudaMemset(x, 0x3c, bytes);  // every word 0x3c3c3c3c: a normal fp32 (0.0115) or int32
+  int best = -1;
+  float best_ms = 0.f;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    chw_plan_s t{};
+    t.device = p->device;
+    t.m = p->m;
+    t.batch = tbatch;
+    t.dtype = p->dtype;
+    t.norm = p->norm;
+    t.flags = p->flags;
+    t.order = p->order;
+    t.total = total;
+    t.d_status = p->d_status;
+    t.rowstack_slots = slots;
+    apply_choice(&t, cands[i]);
+    bool ok = true;
+    for (int w = 0; w < 2 && ok; ++w)
+      ok = run_transform(&t, x, y, tbatch, nullptr, nullptr, nullptr, nullptr, ws, nullptr) == CHW_OK;
+    if (ok) {
+      cudaEventRecord(e0, nullptr);
+      for (int r = 0; r < 5 && ok; ++r)
+        ok = run_transform(&t, x, y, tbatch, nullptr, nullptr, nullptr, nullptr, ws, nullptr) == CHW_OK;
+      cudaEventRecord(e1, nullptr);
+    }
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      release();
+      return fail(CHW_ERR_CUDA, "autotuner: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    float ms = 0.f;
+    int st = 0;
+    cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemset(p->d_status, 0, sizeof(int));
+    if (!ok || st != 0 || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;  // a candidate that fails is not chosen
+    }
+    ms /= 5.f;
+    if (best < 0 || ms < best_ms) {
+      best = static_cast<int>(i);
+      best_ms = ms;
+    }
+  }
+  release();
+  g_err.clear();
+  if (best < 0) return fail(CHW_ERR_CUDA, "autotuner: no candidate ran");
+  apply_choice(p, cands[best]);
+  p->tuned = 1;
+  p->tune_us = best_ms * 1000.f;
+  chw::tune_cache_put(key, cands[best], p->tune_us);
+  if (path != nullptr) chw::tune_cache_save(path);
+  return CHW_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -709,6 +905,15 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     return fail(CHW_ERR_CUDA, "cudaMalloc(status): %s", cudaGetErrorString(e));
   }
   cudaMemset(p->d_status, 0, sizeof(int));
+  if (autotune_requested(flags)) {
+    r = autotune_plan(p);
+    if (r != CHW_OK) {
+      const std::string why = g_err;
+      cudaFree(p->d_status);
+      delete p;
+      return fail(r, "%s", why.c_str());
+    }
+  }
   if (p->tier == kTierRowStack) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -767,6 +972,49 @@ chw_status_t chw_plan_destroy(chw_plan_t p) {
   return CHW_OK;
 }
 
+int chw_tune_candidates(int m, chw_dtype_t dtype, chw_norm_t norm, uint32_t flags, chw_tune_choice_t* out, int cap) {
+  const std::vector<chw::TuneChoice> c = tune_candidates(m, dtype, norm, flags);
+  for (int i = 0; out != nullptr && i < cap && i < static_cast<int>(c.size()); ++i)
+    out[i] = chw_tune_choice_t{c[i].tier, c[i].row_bits, c[i].tile_bits};
+  return static_cast<int>(c.size());
+}
+
+namespace {
+int order_of(uint32_t flags) {
+  return (flags & CHW_FLAG_ORDER_NATURAL) != 0 ? 1 : ((flags & CHW_FLAG_ORDER_SEQUENCY) != 0 ? 2 : 0);
+}
+}  // namespace
+
+chw_status_t chw_tune_cache_put(const char* device, int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm,
+                                uint32_t flags, const chw_tune_choice_t* choice, float us) {
+  if (device == nullptr || choice == nullptr) return fail(CHW_ERR_INVALID_ARG, "NULL device name or choice");
+  if (batch < 1 || m < 0 || m > CHW_MAX_M) return fail(CHW_ERR_INVALID_ARG, "bad m or batch");
+  chw::tune_cache_put(chw::tune_key(device, m, batch, dtype, norm, order_of(flags)),
+                      chw::TuneChoice{choice->tier, choice->row_bits, choice->tile_bits}, us);
+  return CHW_OK;
+}
+
+chw_status_t chw_tune_cache_get(const char* device, int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm,
+                                uint32_t flags, chw_tune_choice_t* choice, float* us) {
+  if (device == nullptr || choice == nullptr) return fail(CHW_ERR_INVALID_ARG, "NULL device name or choice");
+  if (batch < 1 || m < 0 || m > CHW_MAX_M) return fail(CHW_ERR_INVALID_ARG, "bad m or batch");
+  chw::TuneChoice c{};
+  if (!chw::tune_cache_get(chw::tune_key(device, m, batch, dtype, norm, order_of(flags)), &c, us))
+    return fail(CHW_ERR_UNSUPPORTED, "no cached choice for this key");
+  *choice = chw_tune_choice_t{c.tier, c.row_bits, c.tile_bits};
+  return CHW_OK;
+}
+
+int chw_tune_cache_load(const char* path) { return chw::tune_cache_load(path); }
+
+chw_status_t chw_tune_cache_save(const char* path) {
+  if (path == nullptr) return fail(CHW_ERR_INVALID_ARG, "NULL path");
+  if (!chw::tune_cache_save(path)) return fail(CHW_ERR_INVALID_ARG, "cannot write %s", path);
+  return CHW_OK;
+}
+
+void chw_tune_cache_clear(void) { chw::tune_cache_clear(); }
+
 chw_status_t chw_plan_get_info(chw_plan_t p, chw_plan_info_t* info) {
   if (p == nullptr || info == nullptr) return fail(CHW_ERR_INVALID_ARG, "NULL plan or info");
   std::memset(info, 0, sizeof(*info));
@@ -779,11 +1027,14 @@ chw_status_t chw_plan_get_info(chw_plan_t p, chw_plan_info_t* info) {
   info->row_bits = p->row_bits;
   info->cluster = 1;
   info->kernels_per_call = p->passes;
-  if (p->tier == kTierFused || p->tier == kTierCluster) info->cluster = 1 << row_shape(p->m).cb;
-  if (p->tier == kTierTwoPass) info->cluster = 1 << row_shape(p->row_bits).cb;
+  if (p->tier == kTierFused || p->tier == kTierCluster) info->cluster = 1 << row_shape(p->m, p->tile_bits).cb;
+  if (p->tier == kTierTwoPass) info->cluster = 1 << row_shape(p->row_bits, p->tile_bits).cb;
   info->workspace_bytes = static_cast<int64_t>(p->workspace_bytes);
   info->total_elements = p->total;
   info->order = p->order;
+  info->tile_bits = p->tile_bits;
+  info->tuned = p->tuned;
+  info->tune_us = p->tune_us;
   if (p->ragged) {
     info->kernels_per_call = chw::ragged_launches(p->ragged);  // all replayed by one graph launch
     info->workspace_bytes = static_cast<int64_t>(chw::ragged_workspace_bytes(p->ragged));

@@ -1,0 +1,97 @@
+"""Autotuned plans (GPU): the tuner times every candidate, keeps one, caches it, and the
+plan it makes computes the same bits as the oracle's cascade."""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import assert_bitwise
+from paper_1609_06641_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ORACLE_DT = {"f32": np.float32, "i32": np.int32}
+
+
+@pytest.fixture(scope="module")
+def chw(cuda_device, tmp_path_factory):
+    import paper_1609_06641_gb300 as chw
+    from paper_1609_06641_gb300 import build
+
+    build.build()
+    # read once per process, on the first autotuned plan
+    os.environ["CHW_TUNE_CACHE"] = str(tmp_path_factory.mktemp("tune") / "cache.txt")
+    chw.chw_tune_cache_clear()
+    return chw
+
+
+def _x(m, batch, dtype, seed):
+    if dtype == "i32":
+        return W.uniform_int32(m, batch, seed, bound=1 << max(1, 29 - m))
+    return W.normal_f32(m, batch, seed)
+
+
+def _forward(chw, p, x):
+    import torch
+
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    chw.chw_forward(p, xd, yd)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(p) == 0
+    return yd.cpu().numpy()
+
+
+CASES = [
+    (14, 40, "f32", "end", "dyadic"),
+    (16, 24, "f32", "end", "dyadic"),
+    (15, 9, "i32", "none", "sequency"),
+    (17, 6, "f32", "per_level", "dyadic"),
+    (17, 4, "f32", "end", "natural"),
+    (19, 3, "i32", "none", "dyadic"),
+    (21, 2, "f32", "end", "sequency"),
+]
+
+
+@pytest.mark.parametrize("m,batch,dtype,norm,order", CASES)
+def test_autotuned_plan_is_bit_exact_and_cached(chw, m, batch, dtype, norm, order):
+    cands = chw.chw_tune_candidates(m, dtype, norm, order=order)
+    assert len(cands) >= 2
+    p = chw.chw_plan(m, batch, dtype, norm, chw.CHW_FLAG_AUTOTUNE, order=order)
+    info = chw.chw_plan_get_info(p)
+    assert info.tuned == 1 and info.tune_us > 0
+    assert (info.tier, info.row_bits, info.tile_bits) in cands
+    assert info.passes == (2 if info.tier == 3 else 1)
+    x = _x(m, batch, dtype, 9000 + m)
+    y = _forward(chw, p, x)
+    assert_bitwise(y, O.wht_ordered(x, m, order, ORACLE_DT[dtype], norm), f"tuned m={m} {order} {info.tier}")
+    # the same key again: the cached choice, no timing
+    p2 = chw.chw_plan(m, batch, dtype, norm, chw.CHW_FLAG_AUTOTUNE, order=order)
+    i2 = chw.chw_plan_get_info(p2)
+    assert i2.tuned == 2 and (i2.tier, i2.row_bits, i2.tile_bits) == (info.tier, info.row_bits, info.tile_bits)
+    text = open(os.environ["CHW_TUNE_CACHE"]).read()
+    assert f":m{m}:" in text
+
+
+def test_every_candidate_is_bit_exact(chw):
+    # the tuner may pick any candidate, so each must compute the cascade exactly: apply each
+    # one through the cache and run it
+    import torch
+
+    m, batch = 17, 3
+    x = W.normal_f32(m, batch, 9100)
+    ref = O.chw_cascade(x, m, np.float32, "end")
+    dev = torch.cuda.get_device_name(0)
+    for cand in chw.chw_tune_candidates(m, "f32", "end"):
+        chw.chw_tune_cache_put(dev, m, batch, "f32", "end", cand, 1.0)
+        p = chw.chw_plan(m, batch, "f32", "end", chw.CHW_FLAG_AUTOTUNE)
+        info = chw.chw_plan_get_info(p)
+        assert info.tuned == 2 and (info.tier, info.row_bits, info.tile_bits) == cand
+        assert_bitwise(_forward(chw, p, x), ref, f"candidate {cand}")
+
+
+def test_single_configuration_is_not_timed(chw):
+    p = chw.chw_plan(12, 8, "f32", "end", chw.CHW_FLAG_AUTOTUNE)
+    assert chw.chw_plan_get_info(p).tuned == 0
