@@ -451,6 +451,15 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
         kernels_in_graph=int(chw.chw_plan_get_info(pr).kernels_per_call),
         oracle=(lambda: [O.wht_fast_dyadic(h.astype(np.float64), int(ms_arr[i])) for h, i in zip(hr, rsel)],
                 sum(2 * h.nbytes for h in hr), "every 250th signal of the batch, FP64 O2"))
+    # the same ragged batch with each length's configuration picked by the autotuner
+    del pr
+    t0 = time.perf_counter()
+    pt = chw.chw_plan_ragged(ms_arr, "f32", "end", chw.CHW_FLAG_AUTOTUNE)
+    plan_s = time.perf_counter() - t0
+    ms_t = time_device(lambda: chw.chw_forward_ragged(pt, xr, yr), k, warmup, 1, st)
+    it = chw.chw_plan_get_info(pt)
+    rec("ragged_10000_m6to20_f32_autotuned", 2 * useful * 4, ms_t, 1, kernels_in_graph=int(it.kernels_per_call),
+        tuned=int(it.tuned), plan_ms=round(plan_s * 1e3, 1))
     return out
 
 

@@ -82,8 +82,9 @@ typedef enum chw_norm_e {
                                     /* withholds a signal and waits give up after a few    */
                                     /* thousand polls, so chw_last_device_status() reports */
                                     /* CHW_ERR_TIMEOUT; the output is then undefined       */
-#define CHW_FLAG_CLUSTER 128u       /* m = 15, 16: thread-block-cluster (DSMEM) tier instead */
-                                    /* of the tensor-memory tier                           */
+#define CHW_FLAG_CLUSTER 128u       /* m = 15..17: thread-block-cluster (DSMEM) tier instead */
+                                    /* of the tensor-memory tier (15, 16) or the two-pass  */
+                                    /* split (17)                                          */
 #define CHW_FLAG_AUTOTUNE 256u      /* pick the tier, two-pass split and CTA tile by timing */
                                     /* the candidates (chw_tune_candidates) on the device  */
                                     /* when the plan is made; CHW_AUTOTUNE=1 in the        */

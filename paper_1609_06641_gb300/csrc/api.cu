@@ -495,7 +495,8 @@ chw_status_t build_haar_walsh(chw_plan_s* p) {
   }
   std::string why;
   p->hw = chw::ragged_create_at(ms.data(), off.data(), static_cast<int64_t>(ms.size()), p->total,
-                                p->dtype == CHW_I32 ? chw::kVarI32 : fused_variant(p, true), p->d_status, &why);
+                                p->dtype == CHW_I32 ? chw::kVarI32 : fused_variant(p, true), p->d_status, false,
+                                &why);
   if (p->hw == nullptr) return fail(CHW_ERR_CUDA, "Haar-Walsh task set: %s", why.c_str());
   for (int k = chw::kRaggedMaxM + 1; k < m; ++k) {
     chw_status_t r = chw_plan(&p->hw_big[k], k, 1, p->dtype, p->norm, 0);
@@ -874,6 +875,12 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     p->tier = kTierTwoPass;
     p->passes = 2;
     p->row_bits = m - (m >= 23 ? (m - 17 > 6 ? m - 17 : 6) : 6);
+  } else if (m == 17 && p->order == 0 && (flags & (CHW_FLAG_ROWSTACK | CHW_FLAG_CLUSTER | CHW_FLAG_TEST_STALL)) == 0) {
+    // 2^17 words do not fit one SM: the two-pass split (a = 9) measured faster on GB300
+    // than the 8-CTA cluster (3078 vs 2722 GB/s on 2048 signals)
+    p->tier = kTierTwoPass;
+    p->passes = 2;
+    p->row_bits = 8;
   } else if (m <= 17) {
     if (m < 5 && p->total % 32 != 0) {
       p->tier = kTierSimple;
@@ -1256,7 +1263,8 @@ chw_status_t chw_plan_ragged(chw_plan_t* out, const uint8_t* ms_host, int64_t co
   cudaMemset(p->d_status, 0, sizeof(int));
   std::string why;
   p->ragged = chw::ragged_create(ms_host, count, dtype == CHW_I32 ? chw::kVarI32 : fused_variant(p, true),
-                                 p->d_status, &why);
+                                 p->d_status, autotune_requested(flags), &why);
+  if (p->ragged != nullptr && chw::ragged_tuned(p->ragged)) p->tuned = 1;
   if (p->ragged == nullptr) {
     cudaFree(p->d_status);
     delete p;

@@ -21,6 +21,7 @@ struct RaggedGroup {
   int m = 0;
   int64_t count = 0;
   int64_t* d_off = nullptr;  // the group's signal offsets (device)
+  int opt = 0;               // the group's configuration (see group_options)
 };
 
 struct RaggedPlan {
@@ -41,6 +42,7 @@ struct RaggedPlan {
   uint32_t* d_scratch = nullptr;
   int64_t scratch_words = 0;
   int launches = 0;
+  bool tuned = false;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   const void* gx = nullptr;
@@ -85,17 +87,38 @@ float end_scale_host(int m) {  // fp32(2^{-m/2}), as the kernels compute it
   return std::ldexp(r, -(m / 2));
 }
 
-constexpr int kTwoPassA = 9;  // column bits of the two-pass split for m = 18..20
+// Configurations of a length group (RaggedGroup::opt); option 0 is the built-in choice.
+//   m = 13, 14   one: the batched single-CTA kernel.
+//   m = 15, 16   0: clusters of 2^14-word tiles; 1: clusters of 2^13-word tiles.
+//   m = 17       0: 8-CTA cluster; 1: the two-pass split with a = 9.
+//   m = 18..20   the two-pass split with a = 9 (0), 8 (1) or 10 (2) column bits.
+int group_options(int m) {
+  if (m == 15 || m == 16 || m == 17) return 2;
+  if (m >= 18) return 3;
+  return 1;
+}
+
+bool two_pass_opt(int m, int opt) { return m >= 18 || (m == 17 && opt == 1); }
+
+int two_pass_a(int m, int opt) {
+  if (m == 17) return 9;
+  return opt == 1 ? 8 : (opt == 2 ? 10 : 9);
+}
 
 int64_t two_pass_chunk(int m) { return std::max<int64_t>(1, kRaggedScratchWords >> m); }
 
-// Record the launches of one length group on the capture stream.
-cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, const CUtensorMap& tx, const CUtensorMap& ts,
-                         void* y) {
-  cudaStream_t st = r->cap;
+int group_launches(const RaggedGroup& g) {
+  if (!two_pass_opt(g.m, g.opt)) return 1;
+  return static_cast<int>(2 * ((g.count + two_pass_chunk(g.m) - 1) / two_pass_chunk(g.m)));
+}
+
+// Record (or issue) the launches of `count` signals of one length group on stream `st`.
+cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, int64_t count, const CUtensorMap& tx,
+                         const CUtensorMap& ts, void* y, cudaStream_t st) {
   const int m = g.m;
-  if (m <= 17) {
-    const int tb = m == 13 ? 13 : 14, cb = m <= 14 ? 0 : m - 14;
+  if (!two_pass_opt(m, g.opt)) {
+    const int tb = m == 13 ? 13 : ((m == 15 || m == 16) && g.opt == 1 ? 13 : 14);
+    const int cb = m - tb > 0 ? m - tb : 0;
     FusedLaunchFn fn = lookup_fused(0, m, tb, cb, r->variant, 0);
     if (!fn) return cudaErrorInvalidValue;
     FusedArgs a{};
@@ -106,19 +129,20 @@ cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, const CUtens
     a.in_off = g.d_off;
     a.out_off = g.d_off;
     a.sig_shift = 0;
-    return fn(&tx, a, g.count, st);
+    return fn(&tx, a, count, st);
   }
-  // m = 18..20: pass 1 on rows of 2^b (2^(13-b) rows per 2^13-word tile, 2^(m-13) tiles per
-  // signal) into column-blocked scratch; pass 2 on 2^a x 32 column tiles of 2^14 words
-  // (2^(m-14) per signal) written back at the signal's offset.
-  const int A = kTwoPassA, b = m - A;
+  // Two passes: pass 1 on rows of 2^b (2^(13-b) rows per 2^13-word tile, 2^(m-13) tiles per
+  // signal) into column-blocked scratch; pass 2 on 2^a x 32 column tiles (2^(tb+cb) words,
+  // 2^(m-tb-cb) per signal) written back at the signal's offset.
+  const int A = two_pass_a(m, g.opt), b = m - A;
+  const int tb2 = A <= 8 ? 13 : 14, cb2 = A <= 9 ? 0 : A - 9, ub2 = tb2 + cb2;
   const int v1 = r->variant == kVarEnd ? static_cast<int>(kVarPlain) : r->variant;
   FusedLaunchFn f1 = lookup_fused(0, b, 13, 0, v1, 1);
-  FusedLaunchFn f2 = lookup_fused(5, A, 14, 0, r->variant, 0);
+  FusedLaunchFn f2 = lookup_fused(5, A, tb2, cb2, r->variant, 0);
   if (!f1 || !f2) return cudaErrorInvalidValue;
   const int64_t chunk = two_pass_chunk(m);
-  for (int64_t s0 = 0; s0 < g.count; s0 += chunk) {
-    const int64_t cnt = std::min(chunk, g.count - s0);
+  for (int64_t s0 = 0; s0 < count; s0 += chunk) {
+    const int64_t cnt = std::min(chunk, count - s0);
     FusedArgs p1{};
     p1.status = r->d_status;
     p1.out = r->d_scratch;
@@ -135,16 +159,67 @@ cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, const CUtens
     p2.out_total = r->total;
     p2.end_scale = end_scale_host(m);
     p2.out_off = g.d_off + s0;
-    p2.sig_shift = m - 14;
-    e = f2(&ts, p2, cnt << (m - 14), st);
+    p2.sig_shift = m - ub2;
+    e = f2(&ts, p2, cnt << (m - ub2), st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
+// Time every configuration of every group with more than one, on up to 2^26 words of the
+// group's signals (offsets into temporary arrays of the plan's size, CUDA events, one
+// warm-up and the mean of three runs), and keep each group's fastest.  Skipped (built-in
+// choices kept) when the temporary arrays cannot be allocated.
+void tune_groups(RaggedPlan* r) {
+  void *x = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const size_t bytes = static_cast<size_t>(r->total) * 4;
+  if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+  } else {
+    cudaMemset(x, 0x3c, bytes);
+    CUtensorMap tx, ts;
+    const void* sp = r->d_scratch != nullptr ? static_cast<const void*>(r->d_scratch) : x;
+    const int64_t sw = r->d_scratch != nullptr ? r->scratch_words : r->total;
+    if (encode_rows(&tx, x, r->total) && encode_rows(&ts, sp, sw)) {
+      for (RaggedGroup& g : r->groups) {
+        const int nopt = group_options(g.m);
+        if (nopt < 2) continue;
+        const int64_t cnt = std::min<int64_t>(g.count, std::max<int64_t>(1, (int64_t{1} << 26) >> g.m));
+        int best = 0;
+        float best_ms = -1.f;
+        for (int opt = 0; opt < nopt; ++opt) {
+          g.opt = opt;
+          bool ok = launch_group(r, g, cnt, tx, ts, y, r->cap) == cudaSuccess;
+          cudaEventRecord(e0, r->cap);
+          for (int k = 0; k < 3 && ok; ++k) ok = launch_group(r, g, cnt, tx, ts, y, r->cap) == cudaSuccess;
+          cudaEventRecord(e1, r->cap);
+          float ms = 0.f;
+          int st = 0;
+          ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+          cudaMemcpy(&st, r->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+          cudaMemset(r->d_status, 0, sizeof(int));
+          cudaGetLastError();
+          if (ok && st == 0 && (best_ms < 0.f || ms < best_ms)) {
+            best = opt;
+            best_ms = ms;
+          }
+        }
+        g.opt = best;
+      }
+      r->tuned = true;
+    }
+  }
+  if (x) cudaFree(x);
+  if (y) cudaFree(y);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+}
+
 }  // namespace
 
-RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, std::string* why) {
+RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, bool tune, std::string* why) {
   std::vector<int64_t> off(count + 1);
   int64_t o = 0;
   for (int64_t i = 0; i < count; ++i) {
@@ -153,11 +228,11 @@ RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_
     o = (o + 31) & ~int64_t{31};  // every signal starts on a 128-byte boundary
   }
   off[count] = o;
-  return ragged_create_at(ms, off.data(), count, o, variant, d_status, why);
+  return ragged_create_at(ms, off.data(), count, o, variant, d_status, tune, why);
 }
 
 RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t count, int64_t total, int variant,
-                             int* d_status, std::string* why) {
+                             int* d_status, bool tune, std::string* why) {
   auto* r = new RaggedPlan();
   r->count = count;
   r->ms.assign(ms, ms + count);
@@ -200,8 +275,7 @@ RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t 
     e = cudaMalloc(&g.d_off, go.size() * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMemcpy(g.d_off, go.data(), go.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     r->groups.push_back(g);
-    r->launches += m >= 18 ? static_cast<int>(2 * ((g.count + two_pass_chunk(m) - 1) / two_pass_chunk(m))) : 1;
-    if (m >= 18) r->scratch_words = kRaggedScratchWords;
+    if (m >= (tune ? 17 : 18)) r->scratch_words = kRaggedScratchWords;  // two-pass configurations
   }
   if (e == cudaSuccess && r->ntasks > 0) {
     e = cudaMalloc(&r->d_tasks, tasks.size() * sizeof(RaggedTask));
@@ -222,6 +296,17 @@ RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t 
     free_plan(r);
     return nullptr;
   }
+  if (tune && !r->groups.empty()) tune_groups(r);
+  bool scratch = false;
+  for (const RaggedGroup& g : r->groups) {
+    r->launches += group_launches(g);
+    scratch |= two_pass_opt(g.m, g.opt);
+  }
+  if (!scratch && r->d_scratch != nullptr) {  // no two-pass group after all
+    cudaFree(r->d_scratch);
+    r->d_scratch = nullptr;
+    r->scratch_words = 0;
+  }
   return r;
 }
 
@@ -229,6 +314,7 @@ void ragged_destroy(RaggedPlan* r) { free_plan(r); }
 int64_t ragged_total(const RaggedPlan* r) { return r->total; }
 int ragged_passes(const RaggedPlan* r) { return r->scratch_words > 0 ? 2 : 1; }
 int ragged_launches(const RaggedPlan* r) { return r->launches; }
+bool ragged_tuned(const RaggedPlan* r) { return r->tuned; }
 size_t ragged_workspace_bytes(const RaggedPlan* r) { return static_cast<size_t>(r->scratch_words) * sizeof(uint32_t); }
 void ragged_offsets(const RaggedPlan* r, int64_t* out) { std::memcpy(out, r->off.data(), (r->count + 1) * sizeof(int64_t)); }
 
@@ -270,7 +356,7 @@ int ragged_run(RaggedPlan* r, const void* x, void* y, cudaStream_t st, std::stri
         }
       }
       for (const RaggedGroup& grp : r->groups)
-        if (le == cudaSuccess) le = launch_group(r, grp, tx, ts, y);
+        if (le == cudaSuccess) le = launch_group(r, grp, grp.count, tx, ts, y, r->cap);
       e = cudaStreamEndCapture(r->cap, &g);
       if (e == cudaSuccess && le != cudaSuccess) e = le;
     }

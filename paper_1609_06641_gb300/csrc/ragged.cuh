@@ -9,6 +9,8 @@
 //   m = 18-20 the two-pass split y = H_b X^T H_a with a = 9: the first pass reads the
 //             signals at their offsets into plan-owned scratch, the second writes them
 //             back at their offsets, in chunks of signals that fit the scratch.
+// A tuned plan times each length's alternatives when it is made (tile size for 2^15, 2^16;
+// cluster or two passes for 2^17; a = 8, 9 or 10 for 2^18..2^20) and keeps the fastest.
 // The graph is recorded per pair of x/y pointers and replayed by every call with them.
 #pragma once
 
@@ -42,15 +44,18 @@ struct RaggedArgs {
 };
 
 struct RaggedPlan;
-RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, std::string* why);
+// `tune`: time each length group's configurations (tile size, cluster or two passes, the
+// two-pass split) on temporary arrays of the plan's size and keep the fastest.
+RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, bool tune, std::string* why);
 // The same over caller-chosen offsets (elements of x and y; `total` = their length): signals
 // with m >= 13 must start on a 32-element boundary, shorter ones anywhere.
 RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t count, int64_t total, int variant,
-                             int* d_status, std::string* why);
+                             int* d_status, bool tune, std::string* why);
 void ragged_destroy(RaggedPlan* r);
 int64_t ragged_total(const RaggedPlan* r);
 int ragged_passes(const RaggedPlan* r);
 int ragged_launches(const RaggedPlan* r);
+bool ragged_tuned(const RaggedPlan* r);
 size_t ragged_workspace_bytes(const RaggedPlan* r);
 void ragged_offsets(const RaggedPlan* r, int64_t* out);
 int ragged_run(RaggedPlan* r, const void* x, void* y, cudaStream_t st, std::string* why);

@@ -59,10 +59,10 @@ def test_f32_every_m(chw, torch, m, norm):
     if m in (15, 16):
         assert info.tier == 7 and info.cluster == 1  # one CTA per signal, tensor memory
     elif m == 17:
-        assert info.tier == 2 and info.cluster == 8  # thread-block cluster
+        assert info.tier == 3 and info.passes == 2 and info.row_bits == 8  # two passes, a = 9
 
 
-@pytest.mark.parametrize("m", [15, 16])
+@pytest.mark.parametrize("m", [15, 16, 17])
 @pytest.mark.parametrize("norm", ["per_level", "end"])
 def test_cluster_tier_on_request(chw, torch, m, norm):
     x = W.normal_f32(m, 5, seed=140 + m)

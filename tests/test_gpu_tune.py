@@ -95,3 +95,25 @@ def test_every_candidate_is_bit_exact(chw):
 def test_single_configuration_is_not_timed(chw):
     p = chw.chw_plan(12, 8, "f32", "end", chw.CHW_FLAG_AUTOTUNE)
     assert chw.chw_plan_get_info(p).tuned == 0
+
+
+def test_tuned_ragged_plan_is_bit_exact(chw):
+    import torch
+
+    rng = np.random.default_rng(21)
+    ms = np.concatenate([np.full(6, 15), np.full(5, 16), np.full(4, 17), np.full(3, 18), np.full(2, 20),
+                         rng.integers(0, 15, 20)]).astype(np.uint8)
+    rng.shuffle(ms)
+    p = chw.chw_plan_ragged(ms, "f32", "end", chw.CHW_FLAG_AUTOTUNE)
+    assert chw.chw_plan_get_info(p).tuned == 1
+    off = chw.chw_ragged_offsets(p)
+    x = rng.standard_normal(int(off[-1])).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    chw.chw_forward_ragged(p, xd, yd)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(p) == 0
+    y = yd.cpu().numpy()
+    for i, m in enumerate(ms):
+        seg = x[off[i]: off[i] + (1 << int(m))][None, :]
+        assert_bitwise(y[off[i]: off[i] + seg.size], O.chw_cascade(seg, int(m), np.float32, "end")[0], f"signal {i} m={m}")
