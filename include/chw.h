@@ -134,8 +134,12 @@ typedef struct chw_tune_choice_s {
  * y_seq[k] = y[k ^ (k >> 1)] (row k has k sign changes).  The butterflies, and so every
  * value, are those of the dyadic transform; only the store changes.  Both ordered
  * matrices are symmetric, so chw_adjoint of an ordered plan is the same ordered transform
- * (D then applied to its input).  Natural order takes m <= 23 (m >= 15 runs as two HBM
+ * (D then applied to its input).  Natural order takes m <= 23 (m >= 17 runs as two HBM
  * passes); ordered plans cannot be combined with CHW_FLAG_ROWSTACK or ragged plans.
+ * Tiers by m (chw_plan_get_info reports the one chosen): m <= 14 one CTA per tile in
+ * registers and shared memory; m = 15, 16 one SM per signal with the signal held in tensor
+ * memory; m = 17 (dyadic, natural) .. 29 two HBM passes; m = 17 in sequency order a
+ * thread-block cluster.  CHW_FLAG_AUTOTUNE replaces these built-in choices by measured ones.
  * Allocates the plan (host) and its device workspace on the current device.  Returns
  * CHW_ERR_INVALID_ARG / CHW_ERR_UNSUPPORTED / CHW_ERR_OOM / CHW_ERR_CUDA on failure, in
  * which case *plan is set to NULL.
@@ -156,7 +160,9 @@ chw_status_t chw_plan(chw_plan_t* plan, int m, int64_t batch, chw_dtype_t dtype,
  * (signals up to 2^12 share one persistent kernel over a work list; 2^13..2^17 run as
  * batched one-pass launches and 2^18..2^20 as two-pass launches, reading and writing each
  * signal at its own offset); chw_forward_ragged() replays them as one CUDA graph launch.
- * chw_plan_get_info() reports the kernels in the graph (kernels_per_call).
+ * chw_plan_get_info() reports the kernels in the graph (kernels_per_call).  With
+ * CHW_FLAG_AUTOTUNE each length's configuration is timed and chosen when the plan is made
+ * (tuned = 1 in chw_plan_get_info).
  */
 chw_status_t chw_plan_ragged(chw_plan_t* plan, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,
                              chw_norm_t norm, uint32_t flags);
