@@ -242,6 +242,23 @@ chw_status_t validate_data_ptr(const void* p, const char* name) {
   return CHW_OK;
 }
 
+// Let a batched single-CTA launch in dyadic order write each tile with one TMA store (the
+// kernel's tile-store layout) when its outputs are whole tiles and carry no D; otherwise, or
+// if the driver rejects the 4-D view, the tiles go out through the SM.
+void enable_tile_store(chw::FusedArgs* a, void* out, int64_t total, int tlo, int M, int tb, int om) {
+  if (om != 0 || a->diag_out != nullptr || total % (int64_t{1} << tb) != 0) return;
+  auto enc = tensor_map_encoder();
+  if (!enc) return;
+  const int S = chw::stage_key(tlo, M, tb, 0, om);
+  cuuint64_t dims[4] = {32, 8, cuuint64_t{1} << (S - 5), static_cast<cuuint64_t>(total >> (S + 3))};
+  cuuint64_t strides[3] = {cuuint64_t{4} << S, 128, cuuint64_t{4} << (S + 3)};
+  cuuint32_t box[4] = {32, 8, 1u << (S - 5), 1u << (tb - S - 3)};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (enc(&a->tout, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+    a->tma_store = 1;
+}
+
 chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
                              const int8_t* diag_in, const int8_t* diag_out, int64_t diag_mask, int colblock_a,
                              float scale, cudaStream_t st) {
@@ -264,6 +281,7 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
   a.nat_b = 0;
   a.stall_cta = (p->flags & CHW_FLAG_TEST_STALL) != 0 ? 2 : 0;  // rank 1 withholds its signal
   a.wait_tries = (p->flags & CHW_FLAG_TEST_STALL) != 0 ? 4096u : 0u;
+  if (s.cb == 0) enable_tile_store(&a, out, total, 0, M, s.tb, om);
   const int64_t unit = int64_t{1} << (s.tb + s.cb);
   const int64_t units = s.cb > 0 ? total / unit : (total + unit - 1) / unit;
   CHW_CUDA(fn(&map, a, units, st));
@@ -323,6 +341,7 @@ chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, int om, const void* 
   a.colblock_a = 0;
   a.order_m = p->m;
   a.nat_b = p->m - A;
+  if (s.cb == 0) enable_tile_store(&a, out, total, 5, A, s.tb, om);
   const int64_t unit = int64_t{1} << (s.tb + s.cb);
   const int64_t units = s.cb > 0 ? total / unit : (total + unit - 1) / unit;
   CHW_CUDA(fn(&map, a, units, st));

@@ -67,6 +67,10 @@ struct FusedArgs {
   // CHW_ERR_TIMEOUT while every CTA still finishes.
   int stall_cta;
   uint32_t wait_tries;
+  // Output by TMA tensor stores (batched single-CTA tiles in dyadic order, outputs one
+  // contiguous run per tile, no D): `tout` views the output as tile_store_map describes.
+  int tma_store;
+  alignas(64) CUtensorMap tout;
 };
 
 // Element where unit u's input (or output) starts: from a per-signal offset table when
@@ -305,6 +309,34 @@ constexpr int pick_stage_key(const Phase& fw, const Lin& omap, int TB) {
   return 5;
 }
 
+// Tiles whose staged outputs form one contiguous run (dyadic order, single CTA) stage their
+// 128-byte rows permuted so that the staging key -- output bits S..S+2, which XOR the
+// 16-byte chunk index -- becomes the row index's low three bits: the layout of a TMA
+// SWIZZLE_128B box over the 4-D view (32 words, bits S..S+2, bits 5..S-1, bits S+3..) of
+// the output (tile_store_map).  The identity when S = 5.
+constexpr bool tile_store_layout(int OM, int CB) { return OM == 0 && CB == 0; }
+
+constexpr Lin lin_stage_rows(int s) {
+  Lin l = lin_identity();
+  for (int b = 5; b < kMaxBits; ++b) {
+    if (b >= s && b < s + 3) {
+      l.img[b] = 1u << (5 + b - s);
+    } else if (b < s) {
+      l.img[b] = 1u << (b + 3);
+    }
+  }
+  return l;
+}
+
+// Staged position of output o (within a tile) for staging key s: the chunk swizzle, then
+// (tile-store layout) the row permutation of lin_stage_rows.
+__host__ __device__ constexpr uint32_t staged_pos(uint32_t o, int s, bool rows) {
+  uint32_t p = o ^ (((o >> s) & 7u) << 2);
+  if (rows && s > 5)
+    p = (p & 31u) | (((p >> s) & 7u) << 5) | (((p >> 5) & ((1u << (s - 5)) - 1u)) << 8) | ((p >> (s + 3)) << (s + 3));
+  return p;
+}
+
 constexpr FusedPlan make_plan(int TLO, int M, int TB, int CB, int OM) {
   FusedPlan f{};
   const int top = TLO + M;  // one past the last transform bit
@@ -325,6 +357,7 @@ constexpr FusedPlan make_plan(int TLO, int M, int TB, int CB, int OM) {
   f.fw = write_order(fin, f.omap);
   f.stage_s = pick_stage_key(f.fw, f.omap, TB);
   Lin fl = compose(lin_stage(f.stage_s), f.omap);
+  if (tile_store_layout(OM, CB)) fl = compose(lin_stage_rows(f.stage_s), fl);
   for (int i = 0; i < kMaxBits; ++i) fl.img[i] &= (1u << TB) - 1u;
   f.lin_final = fl;
   for (int i = 0; i < 4; ++i) f.rank_shift[i] = 0;
@@ -407,10 +440,11 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
   uint32_t* out = static_cast<uint32_t*>(args.out);
   constexpr int NCH = 1 << (TB - 2);
   constexpr int S = F.stage_s;
+  constexpr bool ROWS = tile_store_layout(OUTMODE, CB);
 #pragma unroll 4
   for (int c = threadIdx.x; c < NCH; c += NT) {
     const uint32_t o = static_cast<uint32_t>(c) << 2;
-    const uint32_t pos = o ^ (((o >> S) & 7u) << 2);
+    const uint32_t pos = staged_pos(o, S, ROWS);
     uint4 q = *reinterpret_cast<const uint4*>(buf + pos);
     const int64_t og = out_base + o;  // position in the staged (dyadic or natural) order
     if (og >= args.out_total) continue;
@@ -567,7 +601,7 @@ __device__ __forceinline__ void phase_3_out(int64_t out_base, const FusedArgs& a
 // `parity`: the input's first element is `in_elem0` (for the adjoint's diagonal) and the
 // outputs start at element `out_base`.  All threads of the CTA call this; it returns with
 // the CTA's output stores issued (a barrier is still needed before `buf` is refilled).
-template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE, bool TS = false>
 __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base, const FusedArgs& args,
                                              uint32_t* buf, uint64_t* bar, uint32_t parity) {
   static_assert(CB == 0, "cluster tiles run in the pipelined cluster kernel");
@@ -641,6 +675,19 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
     store_phase<FW, P2, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
     __syncthreads();
   }
+  if constexpr (TS && tile_store_layout(OUTMODE, CB)) {
+    if (args.tma_store) {
+      // the staged tile goes out as one TMA box (args.tout); every thread orders its staging
+      // writes before the async-proxy read, then one thread issues the store
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tma_store_4d(&args.tout, buf, 0, 0, 0, static_cast<int>(out_base >> (F.stage_s + 3)));
+        bulk_commit_group();
+      }
+      return;
+    }
+  }
   copy_out<TLO, M, TB, CB, BF, OUTMODE>(buf, out_base, 0, args);
 }
 
@@ -671,7 +718,8 @@ constexpr int fused_ctas_per_sm() {
 // overlap the butterflies and the stores of the previous unit.
 template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
 __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
-    fused_kernel(const __grid_constant__ CUtensorMap tin, const FusedArgs args, const int64_t units) {
+    fused_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ FusedArgs args,
+                 const int64_t units) {
   static_assert(CB == 0, "cluster shapes use cluster_kernel");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
@@ -694,13 +742,17 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
     uint32_t* cur = (k & 1) ? buf1 : buf0;
     uint32_t* nxt = (k & 1) ? buf0 : buf1;
     const int64_t un = u + stride;
-    if (threadIdx.x == 0 && un < units) tile_issue<TB>(&tin, row0(un), nxt, bar + ((k + 1) & 1));
-    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE>(elem0(u), unit_elem<TB>(args, args.out_off, u), args, cur,
-                                                     bar + (k & 1), (k >> 1) & 1);
+    if (threadIdx.x == 0 && un < units) {
+      if (args.tma_store) bulk_wait_read();  // the previous unit's TMA store has read `nxt`
+      tile_issue<TB>(&tin, row0(un), nxt, bar + ((k + 1) & 1));
+    }
+    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE, true>(elem0(u), unit_elem<TB>(args, args.out_off, u), args,
+                                                           cur, bar + (k & 1), (k >> 1) & 1);
     __syncthreads();
   }
-  // no TMA load left in flight into shared memory, even after a wait gave up
+  // no TMA load or store left in flight on shared memory, even after a wait gave up
   if (threadIdx.x == 0) {
+    if (args.tma_store) bulk_wait_all();
     for (int b = 0; b < 2 && b < k; ++b) {
       const int kl = b + ((k - 1 - b) / 2) * 2;  // this CTA's last unit on buffer b
       mbar_wait_bounded(bar + b, (kl >> 1) & 1, kWaitTries);

@@ -86,6 +86,10 @@ cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t 
   return cudaLaunchKernelEx(&cfg, kern, *tin, args, units);
 }
 
+// Staging key S of a fused shape (see make_plan): a tile-store launch views its output as
+// 4-D boxes {32 words, 8 (bits S..S+2), 2^(S-5) (bits 5..S-1), 2^(TB-S-3) (bits S+3..)}.
+inline int stage_key(int tlo, int m, int tb, int cb, int om) { return make_plan(tlo, m, tb, cb, om).stage_s; }
+
 // Kernel for one fused shape and variant (nullptr if that shape was not compiled).  The
 // table is generated by the build from its list of shapes, one translation unit per shape.
 FusedLaunchFn lookup_fused(int tlo, int m, int tb, int cb, int var, int om);
