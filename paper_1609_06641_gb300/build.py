@@ -12,6 +12,7 @@ import concurrent.futures as cf
 import hashlib
 import os
 import platform
+import re
 import shutil
 import subprocess
 import sys
@@ -143,17 +144,25 @@ def _digest():
 
 
 # Sources of the batched single-CTA, cluster and tensor-memory kernels (the kernels the
-# benchmark's roofline record names); recorded next to committed DRAM-traffic figures so
-# that a figure is used only while the kernel it was measured on is unchanged.
+# benchmark's roofline record names); their digest (code only, comments removed) is
+# recorded next to committed DRAM-traffic figures so that a figure is used only while the
+# code it was measured on is unchanged.
 KERNEL_SOURCES = ("ptx.cuh", "engine.cuh", "fused.cuh", "launch.cuh", "tmem.cuh", "tmem.cu")
+
+
+def _code_only(text):
+    """Source text without comments and blank lines (a comment edit leaves the code's digest)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
 
 
 def kernel_digest():
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(CSRC, name), "rb") as fh:
+        with open(os.path.join(CSRC, name)) as fh:
             h.update(name.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

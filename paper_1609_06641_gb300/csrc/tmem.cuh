@@ -12,9 +12,12 @@
 // columns per row.  After the R rows the same thread reads them back: for each of its 64
 // register labels it holds the R values that differ only in the row bits, and runs the
 // cascade's last butterflies (bits 14..M-1) in registers, with no exchange between
-// threads or SMs.  Results are staged in shared memory in dyadic output order, one
-// 2^14-value chunk at a time, and written by TMA tensor stores that drain while the SM
-// transforms the next row.
+// threads or SMs.  Results are staged in shared memory, one 2^14-value chunk at a time:
+// in dyadic or natural order they leave by TMA tensor stores that drain while the SM
+// transforms the next row; in sequency order the SM copies each aligned 32-element block
+// to its gray^{-1} block.  Each output chunk of a signal is interleaved with a row of the
+// next signal (alternating tensor-memory column layouts), so every step loads one row and
+// stores one chunk.
 //
 // Tensor memory is 128 lanes x 512 columns x 4 bytes = 256 KB per SM: one 2^16-word
 // signal.  Shared memory holds two 64 KB row buffers (the next rows' TMA loads overlap
