@@ -78,10 +78,12 @@ int cluster_tile_bits() {
 }
 
 // Column bits a of the two-pass split y = H_b X^T H_a for m = 18..29 (b = m - a row bits).
-// Measured on GB300 (fp32, 1 GiB per call): single-CTA tiles in both passes are fastest,
-// with a = 9 (2^9 x 32 column blocks in one CTA); from m = 24 on, where b = m - 9 would
-// need cluster rows, a = 11 (4-CTA column clusters, single-CTA rows up to m = 25) wins,
-// and m = 29 takes a = 12.  CHW_TWO_PASS_A (6..12, m - a in 5..17) overrides it (tuning).
+// Measured on GB300 (fp32, 1 GiB per call): single-CTA tiles in both passes are fastest
+// up to m = 23 (a = 9); beyond, the first pass runs rows of 2^15 or 2^16 words on the
+// tensor-memory kernel, so b = m - a is kept at 15..16 with the column pass as small as
+// that allows: a = max(9, m - 16), at most 12 (m = 24..28: 2939, 2875, 2371, 2260, 1824
+// GB/s against 2414, -, 1900, -, 1500 for the earlier a = 11 splits).  CHW_TWO_PASS_A
+// (6..12, m - a in 5..17) overrides it (tuning).
 int two_pass_col_bits(int m) {
   static const int v = [] {
     const char* e = std::getenv("CHW_TWO_PASS_A");
@@ -89,7 +91,8 @@ int two_pass_col_bits(int m) {
   }();
   if (v >= 6 && v <= 12 && m - v <= 17 && m - v >= 5) return v;
   if (m <= 23) return 9;
-  return m <= 28 ? 11 : 12;
+  const int a = m - 16 > 9 ? m - 16 : 9;
+  return a < 12 ? a : 12;
 }
 
 // One-pass row kernel shape for a transform of M bits; `tb` = preferred CTA tile bits for
@@ -259,9 +262,21 @@ void enable_tile_store(chw::FusedArgs* a, void* out, int64_t total, int tlo, int
     a->tma_store = 1;
 }
 
+chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
+                               int64_t units, int64_t ustride, int64_t ubase, const int8_t* diag_in,
+                               const int8_t* diag_out, float scale, cudaStream_t st, int colblock_a = 0,
+                               int64_t diag_mask = 0);
+
+// The first pass of a two-pass split takes the tensor-memory kernel for rows of 2^15 and
+// 2^16 words (unless the plan asks for 2^13-word cluster tiles).
+bool tmem_row_pass(const chw_plan_s* p, int M, int om) { return om == 1 && (M == 15 || M == 16) && p->tile_bits != 13; }
+
 chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
                              const int8_t* diag_in, const int8_t* diag_out, int64_t diag_mask, int colblock_a,
                              float scale, cudaStream_t st) {
+  if (tmem_row_pass(p, M, om) && diag_out == nullptr)
+    return launch_tmem_units(p, M, 1, var, in, out, total, total >> M, 0, 0, diag_in, nullptr, scale, st, colblock_a,
+                             diag_mask);
   const Shape s = row_shape(M, p->tile_bits);
   chw::FusedLaunchFn fn = chw::lookup_fused(0, M, s.tb, s.cb, var, om);
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no row kernel for M=%d tb=%d cb=%d out=%d", M, s.tb, s.cb, om);
@@ -292,7 +307,8 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
 // words: unit u at element ubase + u * ustride of `in` and `out` (ustride 0: 2^M).
 chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
                                int64_t units, int64_t ustride, int64_t ubase, const int8_t* diag_in,
-                               const int8_t* diag_out, float scale, cudaStream_t st) {
+                               const int8_t* diag_out, float scale, cudaStream_t st, int colblock_a,
+                               int64_t diag_mask) {
   chw::TmemLaunchFn fn = chw::lookup_tmem(M, var, om);
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no tensor-memory kernel for m=%d out=%d", M, om);
   CUtensorMap map, omap;
@@ -307,10 +323,11 @@ chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void
   a.end_scale = scale;
   a.diag_in = diag_in;
   a.diag_out = diag_out;
-  a.diag_mask = (int64_t{1} << M) - 1;
+  a.diag_mask = diag_mask != 0 ? diag_mask : (int64_t{1} << M) - 1;
   a.status = p->d_status;
   a.unit_stride = ustride;
   a.unit_base = ubase;
+  a.colblock_a = colblock_a;
   CHW_CUDA(fn(&map, &omap, a, units, st));
   return CHW_OK;
 }
@@ -1054,7 +1071,8 @@ chw_status_t chw_plan_get_info(chw_plan_t p, chw_plan_info_t* info) {
   info->cluster = 1;
   info->kernels_per_call = p->passes;
   if (p->tier == kTierFused || p->tier == kTierCluster) info->cluster = 1 << row_shape(p->m, p->tile_bits).cb;
-  if (p->tier == kTierTwoPass) info->cluster = 1 << row_shape(p->row_bits, p->tile_bits).cb;
+  if (p->tier == kTierTwoPass)
+    info->cluster = tmem_row_pass(p, p->row_bits, p->order == 1 ? 4 : 1) ? 1 : 1 << row_shape(p->row_bits, p->tile_bits).cb;
   info->workspace_bytes = static_cast<int64_t>(p->workspace_bytes);
   info->total_elements = p->total;
   info->order = p->order;

@@ -95,9 +95,10 @@ inline int stage_key(int tlo, int m, int tb, int cb, int om) { return make_plan(
 FusedLaunchFn lookup_fused(int tlo, int m, int tb, int cb, int var, int om);
 
 // The tensor-memory whole-signal kernel (tmem.cuh) for m = 15, 16 in dyadic (om = 0),
-// natural (om = 2) or sequency (om = 3) order: `tin` maps the input as rows of 32 words
+// column-blocked two-pass rows (om = 1, FusedArgs::colblock_a), natural (om = 2) or
+// sequency (om = 3) order: `tin` maps the input as rows of 32 words
 // (boxes of 256 rows), `tout` the output as rows of 2^(m-8) words with boxes of 32 words x
-// 256 rows (dyadic; unused by sequency order) or rows of 2^(m-6) words with boxes of
+// 256 rows (dyadic; unused by om = 1, 3) or rows of 2^(m-6) words with boxes of
 // 32 x 64 (natural), all SWIZZLE_128B; `units` is the number of signals.  nullptr for
 // other shapes.
 using TmemLaunchFn = cudaError_t (*)(const CUtensorMap* tin, const CUtensorMap* tout, const FusedArgs& args,

@@ -1,5 +1,6 @@
 // Launchers of the tensor-memory whole-signal kernel (tmem.cuh): m = 15, 16, four-byte
-// elements, dyadic, natural or sequency order, every butterfly variant.
+// elements, dyadic, natural or sequency order or the column-blocked rows of a two-pass
+// split, every butterfly variant.
 #include "launch.cuh"
 #include "tmem.cuh"
 
@@ -41,6 +42,7 @@ template <int M>
 TmemLaunchFn tmem_order(int var, int om) {
   switch (om) {
     case 0: return tmem_variant<M, 0>(var);
+    case 1: return tmem_variant<M, 1>(var);
     case 2: return tmem_variant<M, 2>(var);
     case 3: return tmem_variant<M, 3>(var);
     default: return nullptr;

@@ -86,12 +86,13 @@ constexpr bool tmem_natural_lanes_ok(const Phase& p) {
   return seen == 0x1f;
 }
 
-// OM = 0: dyadic order; OM = 2: natural (Sylvester) order, label j stored at j; OM = 3:
-// sequency (Walsh) order, dyadic position p stored at gray^{-1}(p).
+// OM = 0: dyadic order; OM = 1: dyadic rows of the two-pass split's first pass, stored
+// column-blocked (see below); OM = 2: natural (Sylvester) order, label j stored at j;
+// OM = 3: sequency (Walsh) order, dyadic position p stored at gray^{-1}(p).
 template <int M, int OM = 0>
 struct TmemCfg {
   static_assert(M == 15 || M == 16, "tensor memory holds one signal of at most 2^16 words");
-  static_assert(OM == 0 || OM == 2 || OM == 3, "dyadic, natural or sequency order");
+  static_assert(OM >= 0 && OM <= 3, "dyadic, column-blocked, natural or sequency order");
   static constexpr int TB = kTmemTB;
   static constexpr int R = 1 << (M - TB);  // rows per signal
   static constexpr int JW = 64 / R;        // registers per row in one output chunk
@@ -345,27 +346,38 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
           bulk_commit_group();
         }
       } else {
-        // Sequency order scatters the runs (gray^{-1} of their high bits), so the chunk goes
-        // out through the SM: a warp copies four 32-element aligned blocks, and gray^{-1}
-        // maps an aligned block onto an aligned block (reordered inside), so each warp store
-        // is four whole 128-byte lines.
+        // Sequency order scatters the runs (gray^{-1} of their high bits), and the
+        // column-blocked order of the first of two passes sends every 32-element segment of
+        // a row to its own block, so the chunk goes out through the SM: a warp copies four
+        // aligned 32-element blocks, each to one whole 128-byte line (gray^{-1} maps an
+        // aligned block onto an aligned block, reordered inside).
         __syncthreads();
         uint32_t* out = static_cast<uint32_t*>(args.out);
+        // OM = 1: row u is row r = u mod 2^a of signal u / 2^a (a = colblock_a); its element
+        // k goes to signal * 2^(a+M) + (k / 32) 2^(a+5) + 32 r + k mod 32
+        const int64_t u = first + k * stride;
+        const int cba = args.colblock_a;
+        const int64_t cb_base = ((u >> cba) << (cba + M)) + ((u & ((int64_t{1} << cba) - 1)) << 5);
 #pragma unroll 4
         for (int i = static_cast<int>(tid); i < (1 << (TB - 2)); i += kTmemThreads) {
           const uint32_t h = static_cast<uint32_t>(i) >> (TB - 3), run = (static_cast<uint32_t>(i) >> 3) & 255u;
           const uint32_t c8 = static_cast<uint32_t>(i) & 7u;
           uint4 val = *reinterpret_cast<const uint4*>(stage + (h << (TB - 1)) + (run << 5) + ((c8 ^ (run & 7u)) << 2));
-          // dyadic position / 4 within the signal, and its gray^{-1}
+          // dyadic position / 4 within the signal
           const uint32_t p4 = (run << (M - 10)) | static_cast<uint32_t>(16 * q) | (h << 3) | c8;
-          uint32_t g = p4;
-          g ^= g >> 1;
-          g ^= g >> 2;
-          g ^= g >> 4;
-          g ^= g >> 8;
-          g ^= g >> 16;
-          val = (__popc(p4) & 1) ? make_uint4(val.z, val.w, val.y, val.x) : make_uint4(val.x, val.y, val.w, val.z);
-          const int64_t addr = ob + (static_cast<int64_t>(g) << 2);
+          int64_t addr;
+          if constexpr (OM == 1) {
+            addr = cb_base + (static_cast<int64_t>(p4 >> 3) << (cba + 5)) + ((p4 & 7u) << 2);
+          } else {
+            uint32_t g = p4;  // gray^{-1}
+            g ^= g >> 1;
+            g ^= g >> 2;
+            g ^= g >> 4;
+            g ^= g >> 8;
+            g ^= g >> 16;
+            val = (__popc(p4) & 1) ? make_uint4(val.z, val.w, val.y, val.x) : make_uint4(val.x, val.y, val.w, val.z);
+            addr = ob + (static_cast<int64_t>(g) << 2);
+          }
           if (args.diag_out != nullptr) {  // D acts on the stored positions
             const int8_t* d = args.diag_out + (addr & args.diag_mask);
             if constexpr (std::is_same_v<BF, BfI32>) {

@@ -117,3 +117,22 @@ def test_tuned_ragged_plan_is_bit_exact(chw):
     for i, m in enumerate(ms):
         seg = x[off[i]: off[i] + (1 << int(m))][None, :]
         assert_bitwise(y[off[i]: off[i] + seg.size], O.chw_cascade(seg, int(m), np.float32, "end")[0], f"signal {i} m={m}")
+
+
+@pytest.mark.parametrize("m,b", [(21, 15), (22, 16), (24, 15), (24, 16), (25, 16)])
+@pytest.mark.parametrize("dtype,norm", [("f32", "end"), ("f32", "per_level"), ("i32", "none")])
+def test_two_pass_with_tensor_memory_rows(chw, m, b, dtype, norm):
+    # the first pass on rows of 2^15 or 2^16 words runs on the tensor-memory kernel
+    # (column-blocked output); forced through the cache so each split is exercised
+    import torch
+
+    batch = 2
+    choice = (3, b, 14)
+    assert choice in chw.chw_tune_candidates(m, dtype, norm)
+    chw.chw_tune_cache_put(torch.cuda.get_device_name(0), m, batch, dtype, norm, choice, 1.0)
+    p = chw.chw_plan(m, batch, dtype, norm, chw.CHW_FLAG_AUTOTUNE)
+    info = chw.chw_plan_get_info(p)
+    assert info.tuned == 2 and info.row_bits == b and info.cluster == 1
+    x = _x(m, batch, dtype, 9200 + m)
+    y = _forward(chw, p, x)
+    assert_bitwise(y[1:], O.chw_cascade(x[1:], m, ORACLE_DT[dtype], norm), f"m={m} b={b} {dtype} {norm}")
