@@ -70,7 +70,7 @@ struct FusedArgs {
   // Output by TMA tensor stores (batched single-CTA tiles in dyadic order, outputs one
   // contiguous run per tile, no D): `tout` views the output as tile_store_map describes.
   int tma_store;
-  alignas(64) CUtensorMap tout;
+  CUtensorMap tout;  // the type carries the alignment TMA needs
 };
 
 // Element where unit u's input (or output) starts: from a per-signal offset table when

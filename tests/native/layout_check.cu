@@ -1,0 +1,136 @@
+// Host-only check of the staging layouts the kernels' TMA stores rely on, computed with the
+// kernels' own constexpr plans (no GPU): every staged position is hit exactly once and the
+// TMA box that reads it writes the output position the cascade defines.  Prints "ALL OK".
+#include <cstdio>
+#include <vector>
+
+#include "tmem.cuh"
+
+using namespace chw;
+
+static bool g_ok = true;
+#define CHECK(cond, ...)           \
+  do {                             \
+    if (!(cond)) {                 \
+      std::printf(__VA_ARGS__);    \
+      std::printf("\n");           \
+      g_ok = false;                \
+      return;                      \
+    }                              \
+  } while (0)
+
+// Fused single-CTA tile in dyadic order: staged position of label L, and the 4-D box
+// {32 words, bits S..S+2, bits 5..S-1, bits S+3..} with SWIZZLE_128B that the tile store uses.
+template <int TLO, int M, int TB>
+void fused_tile_store() {
+  constexpr FusedPlan F = make_plan(TLO, M, TB, 0, 0);
+  const int S = F.stage_s;
+  const uint32_t N = 1u << TB;
+  std::vector<int> seen(N, 0);
+  for (uint32_t L = 0; L < N; ++L) {
+    const uint32_t o = apply(F.omap, L) & (N - 1);
+    const uint32_t pos = apply(F.lin_final, L);
+    CHECK(pos == staged_pos(o, S, true), "fused TLO=%d M=%d: staged position of L=%u", TLO, M, L);
+    const uint32_t c0 = o & 31u, c1 = (o >> S) & 7u, c2 = (o >> 5) & ((1u << (S - 5)) - 1u), c3 = o >> (S + 3);
+    const uint32_t row = c1 + 8u * c2 + (8u << (S - 5)) * c3;
+    CHECK(row * 32u + ((((c0 >> 2) ^ (row & 7u)) << 2)) + (c0 & 3u) == pos, "fused TLO=%d M=%d: box of o=%u", TLO, M, o);
+    CHECK(c0 + (c1 << S) + (c2 << 5) + (c3 << (S + 3)) == o, "fused: global coordinates of o=%u", o);
+    seen[pos]++;
+  }
+  for (uint32_t i = 0; i < N; ++i) CHECK(seen[i] == 1, "fused TLO=%d M=%d: position %u staged %d times", TLO, M, i, seen[i]);
+  std::printf("fused tile store TLO=%d M=%2d TB=%d S=%2d ok\n", TLO, M, TB, S);
+}
+
+// Thread label bits of phase P (lanes and warps), as the kernels' thread_label computes them.
+uint32_t thread_label_host(const Phase& p, uint32_t lane, uint32_t warp) {
+  return lane_label(p, static_cast<int>(lane)) | warp_label(p, static_cast<int>(warp));
+}
+
+// Tensor-memory kernel, dyadic order: chunk q's staging (two 32-word x 256-row boxes,
+// SWIZZLE_128B) against the dyadic output position bitrev_M(label).
+template <int M>
+void tmem_dyadic() {
+  using T = TmemCfg<M, 0>;
+  const uint32_t n = 1u << M;
+  std::vector<int> out(n, 0);
+  for (int q = 0; q < T::R; ++q) {
+    std::vector<int64_t> stage(1u << kTmemTB, -1);
+    for (uint32_t warp = 0; warp < 8; ++warp)
+      for (uint32_t lane = 0; lane < 32; ++lane) {
+        const uint32_t tl = thread_label_host(T::P3, lane, warp);
+        const uint32_t rho = bitrev_bits(tl, 8), sxor = (rho & 7u) << 2;
+        for (int c = 0; c < 16; ++c)
+          for (int e = 0; e < 4; ++e) {
+            const int si = T::src(q, 4 * c + e);
+            const int r = si / T::JW, j = si % T::JW;
+            const uint32_t label = tl | reg_label(T::P3, q * T::JW + j) | (static_cast<uint32_t>(r) << kTmemTB);
+            const uint32_t p = ((c >> 3) << (kTmemTB - 1)) + (((rho << 5) | (4u * (c & 7))) ^ sxor) + e;
+            CHECK(stage[p] < 0, "tmem M=%d q=%d: staged twice at %u", M, q, p);
+            stage[p] = label;
+          }
+      }
+    for (uint32_t h = 0; h < 2; ++h)
+      for (uint32_t row = 0; row < 256; ++row)
+        for (uint32_t x = 0; x < 32; ++x) {
+          const uint32_t sm = (h << (kTmemTB - 1)) + row * 32u + ((((x >> 2) ^ (row & 7u))) << 2) + (x & 3u);
+          const uint32_t pos = (row << (M - 8)) + 64u * q + 32u * h + x;
+          CHECK(stage[sm] >= 0 && pos == bitrev_bits(static_cast<uint32_t>(stage[sm]), M), "tmem M=%d: box of pos %u", M, pos);
+          out[pos]++;
+        }
+  }
+  for (uint32_t i = 0; i < n; ++i) CHECK(out[i] == 1, "tmem M=%d: output %u written %d times", M, i, out[i]);
+  std::printf("tmem dyadic M=%d ok\n", M);
+}
+
+// Tensor-memory kernel, natural order: eight 32-word x 64-row boxes per chunk.
+template <int M>
+void tmem_natural() {
+  using T = TmemCfg<M, 2>;
+  const uint32_t n = 1u << M;
+  std::vector<int> out(n, 0);
+  for (int q = 0; q < T::R; ++q) {
+    const uint32_t qo = T::nat_qo(0, q * T::JW);
+    std::vector<int64_t> stage(1u << kTmemTB, -1);
+    for (uint32_t warp = 0; warp < 8; ++warp)
+      for (uint32_t lane = 0; lane < 32; ++lane) {
+        const uint32_t tl = thread_label_host(T::P3, lane, warp);
+        for (int ii = 0; ii < 64; ++ii) {
+          const int r = ii / T::JW, j = ii % T::JW;
+          const uint32_t psi = T::nat_psi(r, q * T::JW + j);
+          const uint32_t p = ((tl >> 5) << 11) + (tl & 3u) + ((psi << 5) | (((((tl >> 2) & 7u)) ^ (psi & 7u)) << 2));
+          CHECK(stage[p] < 0, "tmem natural M=%d: staged twice at %u", M, p);
+          stage[p] = tl | T::nat_high(r, q * T::JW + j);
+        }
+      }
+    for (uint32_t b = 0; b < 8; ++b)
+      for (uint32_t row = 0; row < 64; ++row)
+        for (uint32_t x = 0; x < 32; ++x) {
+          const uint32_t sm = (b << 11) + row * 32u + ((((x >> 2) ^ (row & 7u))) << 2) + (x & 3u);
+          const uint32_t pos = (row << (M - 6)) + qo * 256u + 32u * b + x;
+          CHECK(stage[sm] >= 0 && pos == static_cast<uint32_t>(stage[sm]), "tmem natural M=%d: box of pos %u", M, pos);
+          out[pos]++;
+        }
+  }
+  for (uint32_t i = 0; i < n; ++i) CHECK(out[i] == 1, "tmem natural M=%d: output %u written %d times", M, i, out[i]);
+  std::printf("tmem natural M=%d ok\n", M);
+}
+
+int main() {
+  fused_tile_store<0, 0, 13>();
+  fused_tile_store<0, 3, 13>();
+  fused_tile_store<0, 7, 13>();
+  fused_tile_store<0, 10, 13>();
+  fused_tile_store<0, 11, 13>();
+  fused_tile_store<0, 12, 13>();
+  fused_tile_store<0, 13, 13>();
+  fused_tile_store<0, 14, 14>();
+  fused_tile_store<5, 6, 13>();
+  fused_tile_store<5, 8, 13>();
+  fused_tile_store<5, 9, 14>();
+  tmem_dyadic<15>();
+  tmem_dyadic<16>();
+  tmem_natural<15>();
+  tmem_natural<16>();
+  std::printf(g_ok ? "ALL OK\n" : "FAILED\n");
+  return g_ok ? 0 : 1;
+}
