@@ -9,7 +9,6 @@ the oracle, never in the CUDA path.
 import numpy as np
 import pytest
 
-import oracle as O
 import oracle.definitions as D
 import oracle.transforms as T
 from conftest import load_golden_matrices, load_golden_table
