@@ -15,7 +15,9 @@ Walsh-Hadamard Transform", arXiv 1609.06641):
   eq. (4), and the closed form of H_m's entries derived from eq. (1).  FP64 / int64.
 * ``transforms``   -- the transform itself in three independent ways: the dense
   matvec (O1), a textbook natural-order fast WHT followed by a bit-reversal
-  reorder (O2), and the closed form one entry at a time (O3); plus the CHW
+  reorder (O2), and the closed form one entry at a time (O3, also vectorised over
+  sampled outputs for sparse inputs, for signals too long to transform on the
+  host); plus the CHW
   cascade of Theorem 1 taken literally in stage order (O4, any dtype, with an
   operation counter for Lemma 1 / Theorem 2) and its transpose, the reversed
   cascade of inverse Haar transforms.
@@ -43,6 +45,7 @@ from .transforms import (
     wht_dense,
     wht_fast_dyadic,
     wht_closed_form,
+    wht_sparse_closed_form,
     haar_analysis,
     haar_synthesis,
     chw_cascade,
@@ -67,6 +70,7 @@ __all__ = [
     "wht_dense",
     "wht_fast_dyadic",
     "wht_closed_form",
+    "wht_sparse_closed_form",
     "haar_analysis",
     "haar_synthesis",
     "chw_cascade",

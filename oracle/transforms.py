@@ -136,6 +136,26 @@ def wht_closed_form(x, m, ks, normalised=True):
     return np.array(out)
 
 
+def wht_sparse_closed_form(js, cs, m, ks, normalised=True):
+    """O3 for a sparse input: outputs y[k], k in ``ks``, of y = H_m x where x has the value
+    cs[i] at position js[i] and zeros elsewhere, from the closed form of eq. (1)'s entries,
+    H_m[k][j] = 2^{-m/2} (-1)^popcount(bitrev_m(k) & j), vectorised over the outputs.
+
+    With integer ``cs`` and normalised=False the result is the exact int64 sum
+    sum_i cs[i] (-1)^popcount(bitrev_m(k) & js[i]) (the unnormalised transform).  Cost is
+    O(len(js) * len(ks)), so very long signals can be checked at sampled outputs.
+    """
+    k = np.asarray(ks, dtype=np.uint64)
+    rk = np.zeros_like(k)
+    for b in range(m):  # bitrev_m(k), bit by bit
+        rk |= ((k >> np.uint64(b)) & np.uint64(1)) << np.uint64(m - 1 - b)
+    out = np.zeros(k.shape, dtype=np.int64 if not normalised else np.float64)
+    for j, c in zip(js, cs):
+        sign = 1 - 2 * (np.bitwise_count(rk & np.uint64(j)).astype(np.int64) & 1)
+        out += sign * (c if not normalised else float(c))
+    return out * (2.0 ** (-m / 2.0)) if normalised else out
+
+
 # ---------------------------------------------------------------- O4: the CHW cascade
 def haar_analysis(v, c=None, counter=None):
     """Psi_L v along the last axis (eq. (2)); length 2^L.

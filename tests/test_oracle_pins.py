@@ -296,3 +296,31 @@ def test_lowp_reference_properties(fmt, gate):
     ref = O.wht_fast_dyadic(O.dequantise(bits, e_in, fmt), m)
     err = O.rel_err_per_signal(O.dequantise(qb, e_out, fmt)[:5], ref[:5])
     assert err.max() < gate
+
+
+# ---------------------------------------------------------------- O3 on sparse inputs
+@pytest.mark.parametrize("m", [0, 1, 3, 6, 10])
+def test_sparse_closed_form_matches_dense_matrix(m):
+    rng = np.random.default_rng(90 + m)
+    n = 1 << m
+    js = rng.choice(n, size=min(n, 5), replace=False)
+    cs = rng.integers(-7, 8, size=len(js))
+    x = np.zeros(n, dtype=np.int64)
+    x[js] = cs
+    h = O.hadamard_dyadic(m, normalised=False)  # integer rows of eq. (1)
+    ks = np.arange(n)
+    assert np.array_equal(O.wht_sparse_closed_form(js, cs, m, ks, normalised=False), h @ x)
+    got = O.wht_sparse_closed_form(js, cs, m, ks)
+    assert np.allclose(got, O.hadamard_dyadic(m) @ x, rtol=0, atol=1e-12)
+
+
+def test_sparse_closed_form_sampled_outputs_agree_with_fast_wht():
+    m = 14
+    rng = np.random.default_rng(7)
+    js = rng.choice(1 << m, size=6, replace=False)
+    cs = rng.integers(-100, 101, size=6)
+    x = np.zeros((1, 1 << m), dtype=np.int64)
+    x[0, js] = cs
+    full = O.wht_fast_dyadic(x, m, normalised=False)[0]
+    ks = rng.integers(0, 1 << m, 500)
+    assert np.array_equal(O.wht_sparse_closed_form(js, cs, m, ks, normalised=False), full[ks])
