@@ -88,7 +88,7 @@ class ClockSampler:
         0x100: "display_clock_setting",
     }
 
-    def __init__(self, index, period=0.005):
+    def __init__(self, index, period=0.001):
         self.samples = []
         self.period = period
         self.ok = False
@@ -337,14 +337,27 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
         oracle=(lambda: O.wht_fast_dyadic(hi.astype(np.int64), M, normalised=False), 2 * hi.nbytes,
                 "2 signals, int64 fast WHT (O2)"))
     del xi, yi
-    # long signals: two HBM passes
+    # long signals (m = 26 x 4, m = 28 x 1, Uniform(-1,1) from seed 3): two HBM passes; the
+    # round trip H^T H x against x on every signal (FP64 norms; the forward's bitwise parity
+    # with the oracle's cascade at these sizes is a GPU test, too slow for the host here)
     for m, b in ((26, 4), (28, 1)):
-        xl = torch.rand(b, 1 << m, device=dev, generator=g) * 2 - 1
+        xh_l = W.uniform_pm1_f32(m, b, 3)
+        xl = torch.from_numpy(xh_l).to(dev)
         yl = torch.empty_like(xl)
         pl = chw.chw_plan(m, b, "f32", "end")
+        il = chw.chw_plan_get_info(pl)
         ms = time_device(lambda: chw.chw_forward(pl, xl, yl), k, warmup, 1, st)
-        rec(f"m{m}_b{b}_f32_two_pass", 2 * xl.numel() * 4, ms, 2,
-            dram_pass_frac=round(gbs(4 * xl.numel() * 4, ms / 1e3) / peak, 4))
+        back = torch.empty_like(xl)
+        chw.chw_adjoint(pl, yl, back)
+        torch.cuda.synchronize()
+        assert chw.chw_last_device_status(pl) == 0
+        xd64 = xl.double()
+        rt = float(((back.double() - xd64).norm(dim=1) / xd64.norm(dim=1)).max())
+        del back, xd64
+        kw = {"row_bits": int(il.row_bits), "roundtrip_rel_err_max": rt, "roundtrip_gate": 1e-6,
+              "inputs": "Uniform(-1,1) fp32, numpy PCG64 seed 3"}
+        rec(f"m{m}_b{b}_f32_two_pass", 2 * xl.numel() * 4, ms, il.kernels_per_call,
+            dram_pass_frac=round(gbs(2 * il.passes * xl.numel() * 4, ms / 1e3) / peak, 4), **kw)
         del xl, yl, pl
     # autotuned plans (the tuner times every candidate configuration when the plan is made):
     # the built-in choice and the tuned one, side by side
@@ -361,19 +374,48 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
                 row_bits=int(ia.row_bits), tile_bits=int(ia.tile_bits), plan_ms=round(plan_s * 1e3, 1))
             del pa
         del xa, ya
-    # 16-bit storage, m = 12, batch 16384
+    # 16-bit storage, m = 12, batch 16384, on the precision workload: Student-t(3) x per-signal
+    # lognormal(0, 2) from seed 4, stored as (codes, power-of-two exponent).  Errors per
+    # signal on every 8th signal: the dequantised result against the FP64 oracle of the
+    # dequantised input, and against the plain fp32 path on this GPU (same input values).
+    x4 = W.heavy_tailed_f64(12, 16384, 4)
+    sel = np.arange(0, 16384, 8)
     for fmt, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
-        xq = (torch.randn(16384, 1 << 12, device=dev, generator=g)).to(tdt)
+        codes, e_in = W.quantise_pow2(x4, fmt)
+        xq = torch.from_numpy(codes.view(np.int16)).to(dev).view(tdt)
         yq = torch.empty_like(xq)
-        ei = torch.zeros(16384, dtype=torch.int32, device=dev)
+        ei = torch.from_numpy(e_in).to(dev)
         eo = torch.empty_like(ei)
         pq = chw.chw_plan(12, 16384, fmt, "end")
         ms = time_device(lambda: chw.chw_forward(pq, xq, yq, ei, eo), k, warmup, 1, st)
-        cq, eq = W.quantise_pow2(W.heavy_tailed_f64(12, 16, 16), fmt)
+        torch.cuda.synchronize()
+        assert chw.chw_last_device_status(pq) == 0
+        q_out = yq.view(torch.int16).cpu().numpy().view(np.uint16)[sel]
+        e_out = eo.cpu().numpy()[sel]
+        # the plain fp32 path on the same (dequantised) input values
+        t0 = time.perf_counter()
+        deq_in = O.dequantise(codes[sel], e_in[sel], fmt)
+        ref = O.wht_fast_dyadic(deq_in, 12)
+        o_s = time.perf_counter() - t0
+        x32 = torch.from_numpy(deq_in.astype(np.float32)).to(dev)
+        y32 = torch.empty_like(x32)
+        p32 = chw.chw_plan(12, len(sel), "f32", "end")
+        chw.chw_forward(p32, x32, y32)
+        got = O.dequantise(q_out, e_out, fmt)
+        err = O.rel_err_per_signal(got, ref)
+        err32 = O.rel_err_per_signal(got, y32.cpu().numpy())
+        err_f32_path = O.rel_err_per_signal(y32.cpu().numpy(), ref)
         rec(f"m12_b16384_{fmt}", 2 * xq.numel() * 2, ms, 1,
-            oracle=(lambda: O.lowp_forward_reference(cq, eq, 12, fmt, "end"), 2 * cq.nbytes,
-                    "16 signals, fp32 cascade of the codes + exponent rule"))
-        del xq, yq
+            rel_err_vs_fp64_oracle={"max": float(err.max()), "p99": float(np.percentile(err, 99))},
+            rel_err_vs_gpu_fp32_path={"max": float(err32.max()), "p99": float(np.percentile(err32, 99))},
+            gpu_fp32_path_rel_err_vs_fp64={"max": float(err_f32_path.max())},
+            error_gate={"bf16": 1e-2, "f16": 2e-3}[fmt],
+            error_sample=f"every 8th signal ({len(sel)} of 16384)",
+            inputs="Student-t(3) x lognormal(0,2) per signal, numpy PCG64 seed 4, (codes, 2^e) per signal",
+            **{"cpu_oracle_GB/s": round(gbs(2 * len(sel) * 4096 * 2, o_s), 4),
+               "cpu_oracle_sample": f"{len(sel)} signals, FP64 O2 of the dequantised input"})
+        del xq, yq, x32, y32, p32
+    del x4
     # D H_m layer, m = 14, batch 512: forward and adjoint
     xd = torch.randn(512, 1 << 14, device=dev, generator=g)
     yd = torch.empty_like(xd)
@@ -404,9 +446,10 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     rec("m16_b4096_f32_haar_walsh", 2 * nb, ms, 3,
         oracle=(lambda: O.haar_walsh(h16, M, np.float32, "per_level"), nb16, "2 signals, fp32 stages 1..m-1"))
     ms = time_device(lambda: chw.chw_forward_haar(ph, xh, yh, zh), k, warmup, 1, st)
-    rec("m16_b4096_f32_forward_with_haar_output", 3 * nb, ms, 5,
-        oracle=(lambda: O.haar_walsh(O.haar_forward(h16, M, np.float32, "per_level"), M, np.float32, "per_level"),
-                3 * h16.nbytes, "2 signals, fp32 Haar then stages 1..m-1"))
+    rec("m16_b4096_f32_forward_with_haar_output", 3 * nb, ms, 1,
+        bytes_counted="x read once, y and z written once (3 n 4 bytes per signal)",
+        oracle=(lambda: (O.chw_cascade(h16, M, np.float32, "per_level"), O.haar_forward(h16, M, np.float32, "per_level")),
+                3 * h16.nbytes, "2 signals, fp32 cascade and fp32 Haar"))
     del xh, zh, yh, ph
     # natural and sequency output orders on the headline shape and at m = 12
     for order in ("natural", "sequency"):
@@ -445,12 +488,31 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     ms_pm = time_device(per_m, k, warmup, 1, st)
     rec("ragged_10000_as_per_m_launches", 2 * useful * 4, ms_pm, len(groups))
     del groups
-    rsel = [i for i in range(len(ms_arr)) if i % 250 == 0][:40]
-    hr = [W.normal_f32(int(ms_arr[i]), 1, 17 + i) for i in rsel]
+    # errors on every 250th signal: against the FP64 oracle, and against the plain fp32 path
+    # (a one-signal batched plan of the same length on this GPU, same input values)
+    rsel = list(range(0, len(ms_arr), 250))
+    roff = chw.chw_ragged_offsets(pr)
+    hr, got_r, plain_r = [], [], []
+    for i in rsel:
+        mi, o = int(ms_arr[i]), int(roff[i])
+        xi = xr[o: o + (1 << mi)].view(1, -1)
+        yi = torch.empty_like(xi)
+        chw.chw_forward(chw.chw_plan(mi, 1, "f32", "end"), xi, yi)
+        hr.append(xi.cpu().numpy())
+        got_r.append(yr[o: o + (1 << mi)].view(1, -1).cpu().numpy())
+        plain_r.append(yi.cpu().numpy())
+    t0 = time.perf_counter()
+    refs_r = [O.wht_fast_dyadic(h.astype(np.float64), int(ms_arr[i])) for h, i in zip(hr, rsel)]
+    o_s = time.perf_counter() - t0
+    err_r = max(float(O.rel_err_per_signal(g, r).max()) for g, r in zip(got_r, refs_r))
+    err_p = max(float(O.rel_err_per_signal(g, r).max()) for g, r in zip(got_r, plain_r))
+    same = all(np.array_equal(g.view(np.uint32), r.view(np.uint32)) for g, r in zip(got_r, plain_r))
     rec("ragged_10000_m6to20_f32", 2 * useful * 4, ms, 1, elements=useful,
         kernels_in_graph=int(chw.chw_plan_get_info(pr).kernels_per_call),
-        oracle=(lambda: [O.wht_fast_dyadic(h.astype(np.float64), int(ms_arr[i])) for h, i in zip(hr, rsel)],
-                sum(2 * h.nbytes for h in hr), "every 250th signal of the batch, FP64 O2"))
+        rel_err_vs_fp64_oracle_max=err_r, rel_err_vs_gpu_fp32_path_max=err_p, bitwise_equal_to_fp32_path=same,
+        error_gate=1e-6, error_sample=f"every 250th signal ({len(rsel)} signals)",
+        **{"cpu_oracle_GB/s": round(gbs(sum(2 * h.nbytes for h in hr), o_s), 4),
+           "cpu_oracle_sample": "every 250th signal of the batch, FP64 O2"})
     # the same ragged batch with each length's configuration picked by the autotuner
     del pr
     t0 = time.perf_counter()
@@ -461,6 +523,34 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     rec("ragged_10000_m6to20_f32_autotuned", 2 * useful * 4, ms_t, 1, kernels_in_graph=int(it.kernels_per_call),
         tuned=int(it.tuned), plan_ms=round(plan_s * 1e3, 1))
     return out
+
+
+def quick_other(args, chw, torch, dev, peak):
+    """--quick with another storage type, normalisation or output order: one plan, device
+    inputs, CUDA-event timing only (the profiling runs of the other kernels)."""
+    m, batch = args.m, args.batch
+    g = torch.Generator(device=dev).manual_seed(9)
+    ebytes = 2 if args.dtype in ("bf16", "f16") else 4
+    if args.dtype == "i32":
+        x = torch.randint(-(2**14), 2**14 + 1, (batch, 1 << m), device=dev, dtype=torch.int32, generator=g)
+    else:
+        x = torch.randn(batch, 1 << m, device=dev, generator=g)
+        if ebytes == 2:
+            x = x.to(torch.bfloat16 if args.dtype == "bf16" else torch.float16)
+    y = torch.empty_like(x)
+    exps = ()
+    if ebytes == 2:
+        exps = (torch.zeros(batch, dtype=torch.int32, device=dev), torch.empty(batch, dtype=torch.int32, device=dev))
+    norm = "none" if args.dtype == "i32" else args.norm
+    plan = chw.chw_plan(m, batch, args.dtype, norm, args.flags, order=args.order)
+    info = chw.chw_plan_get_info(plan)
+    ms = time_device(lambda: chw.chw_forward(plan, x, y, *exps), args.steps, args.warmup, 1,
+                     torch.cuda.current_stream())
+    assert chw.chw_last_device_status(plan) == 0
+    v = gbs(2 * batch * (1 << m) * ebytes, ms / 1e3)
+    print(json.dumps({"op": "forward", "m": m, "batch": batch, "dtype": args.dtype, "norm": norm,
+                      "order": args.order, "tier": int(info.tier), "ms_per_step": ms, "GB/s": v,
+                      "frac": v / peak}), flush=True)
 
 
 # ---------------------------------------------------------------- main
@@ -476,8 +566,14 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="transform bits of the timed workload")
     ap.add_argument("--batch", type=int, default=BATCH, help="signals of the timed workload")
     ap.add_argument("--flags", type=int, default=0, help="chw_plan flags (e.g. 4: row-stack tier for m = 15..17)")
-    ap.add_argument("--op", default="forward", choices=["forward", "haar", "haar_inverse", "haar_walsh"],
+    ap.add_argument("--op", default="forward", choices=["forward", "haar", "haar_inverse", "haar_walsh", "forward_haar"],
                     help="with --quick: the call timed (profiling runs of the other kernels)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "i32", "bf16", "f16"],
+                    help="with --quick: storage type of the timed forward (profiling runs)")
+    ap.add_argument("--norm", default="end", choices=["end", "per_level", "none"],
+                    help="with --quick: normalisation of the timed forward")
+    ap.add_argument("--order", default="dyadic", choices=["dyadic", "natural", "sequency"],
+                    help="with --quick: output order of the timed forward")
     args = ap.parse_args()
     world, rank, local = dist_env()
 
@@ -510,6 +606,9 @@ def main():
     peak, peak_kind = load_peaks()
 
     m, batch = args.m, args.batch
+    if args.quick and (args.dtype != "f32" or args.norm != "end" or args.order != "dyadic"):
+        quick_other(args, chw, torch, dev, peak)
+        return
     x_host = W.normal_f32(m, batch, SEED + rank)  # each rank its own signals
     x = torch.from_numpy(x_host).to(dev)
     y = torch.empty_like(x)
@@ -518,11 +617,16 @@ def main():
     info = chw.chw_plan_get_info(plan)
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
-    call = {"forward": chw.chw_forward, "haar": chw.chw_haar, "haar_inverse": chw.chw_haar_inverse,
-            "haar_walsh": chw.chw_from_haar}[args.op if args.quick else "forward"]
+    op = args.op if args.quick else "forward"
+    if op == "forward_haar":  # y and the Haar side output z: x read once, y and z written
+        z = torch.empty_like(x)
+        call = lambda p, a, b: chw.chw_forward_haar(p, a, b, z)  # noqa: E731
+    else:
+        call = {"forward": chw.chw_forward, "haar": chw.chw_haar, "haar_inverse": chw.chw_haar_inverse,
+                "haar_walsh": chw.chw_from_haar}[op]
     ms = time_device(lambda: call(plan, x, y), args.steps, args.warmup, world, stream, sampler)
     ms_max = max_over_ranks(ms, world, dev)
-    step_bytes = 2 * batch * (1 << m) * 4
+    step_bytes = (3 if op == "forward_haar" else 2) * batch * (1 << m) * 4
     value = world * gbs(step_bytes, ms_max / 1e3)
     assert chw.chw_last_device_status(plan) == 0
     if args.quick:
@@ -546,6 +650,20 @@ def main():
     e2e_s = max_over_ranks(e2e_s, world, dev)
     if not torch.equal(yh, y.cpu()):
         raise RuntimeError("host-buffer path disagrees with the device path")
+    # the host link alone: the same bytes copied in and out at once (pinned, two streams,
+    # no transform), the bound of the e2e number
+    xd_link = torch.empty_like(x)
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(s_in):
+            xd_link.copy_(xh, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            yh.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    link_s = (time.perf_counter() - t0) / e2e_steps
+    del xd_link
 
     if rank != 0:
         if world > 1:
@@ -590,6 +708,8 @@ def main():
             "d2h_bytes_per_step": BATCH * (1 << M) * 4,
             "ms_per_step": round(e2e_s * 1e3, 3),
             "api": "chw_forward_host (pinned host buffers, 64 MiB chunks over 3 streams)",
+            "host_link_GB/s": round(gbs(step_bytes, link_s), 1),
+            "host_link_note": "the same bytes copied host->device and device->host at once, pinned, no transform",
         },
         "gpu_launches": args.steps * info.kernels_per_call,
         "clocks": sampler.summary(),

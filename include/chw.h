@@ -89,6 +89,22 @@ typedef enum chw_norm_e {
                                     /* the candidates (chw_tune_candidates) on the device  */
                                     /* when the plan is made; CHW_AUTOTUNE=1 in the        */
                                     /* environment turns it on for every plan              */
+#define CHW_FLAG_CHECKED 512u       /* checked mode: the kernels that compute global indices */
+                                    /* from offsets (tiles, tensor-memory rows and columns, */
+                                    /* two-pass scratch, ragged offset tables) range-check  */
+                                    /* every input tile and output address before using it; */
+                                    /* a bad one is skipped and latches                     */
+                                    /* CHW_ERR_DEVICE_CHECK with the offending element index */
+                                    /* (chw_last_device_status, chw_last_error_message); the */
+                                    /* output is then undefined.  Results are otherwise      */
+                                    /* identical; the checks cost a few instructions per     */
+                                    /* store                                                 */
+#define CHW_FLAG_TEST_CORRUPT 1024u /* test hook, ragged plans, only with CHW_FLAG_CHECKED  */
+                                    /* (else CHW_ERR_INVALID_ARG): the plan overwrites, on   */
+                                    /* the host before upload, the offset of its first       */
+                                    /* signal with m >= 13 and of its first signal with      */
+                                    /* m <= 12 by an element index past the end of x and y,  */
+                                    /* so the device checks must catch them                  */
 
 typedef struct chw_plan_s* chw_plan_t;
 
@@ -167,6 +183,20 @@ chw_status_t chw_plan(chw_plan_t* plan, int m, int64_t batch, chw_dtype_t dtype,
 chw_status_t chw_plan_ragged(chw_plan_t* plan, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,
                              chw_norm_t norm, uint32_t flags);
 
+/*
+ * chw_plan_ragged_at -- as chw_plan_ragged, with the caller's own layout: signal i occupies
+ * elements [offsets_host[i], offsets_host[i] + 2^{ms[i]}) of x and y, which hold `total`
+ * elements.  Validated on the host before anything is uploaded: every signal must lie in
+ * [0, total) and no two may overlap (CHW_ERR_INVALID_ARG otherwise), and signals with
+ * m >= 13 must start on a 32-element (128-byte) boundary, because their kernels load them
+ * as rows of 32 words by TMA (CHW_ERR_ALIGNMENT otherwise); shorter signals may start
+ * anywhere.  Elements outside every signal are neither read into results nor written.
+ * The offsets are copied into the plan's device tables, which the recorded CUDA graph
+ * reads, so a call does not take offsets of its own.
+ */
+chw_status_t chw_plan_ragged_at(chw_plan_t* plan, const uint8_t* ms_host, const int64_t* offsets_host, int64_t count,
+                                int64_t total, chw_dtype_t dtype, chw_norm_t norm, uint32_t flags);
+
 /* Element offsets of a ragged plan's signals: offsets_host[0..count] (count+1 entries). */
 chw_status_t chw_ragged_offsets(chw_plan_t plan, int64_t* offsets_host);
 
@@ -237,9 +267,13 @@ chw_status_t chw_haar_inverse(chw_plan_t plan, const void* z, void* x, void* str
  * fp32(2^{-k/2}).  In-place (z == y) allowed.  The plan must have been made with
  * CHW_FLAG_HAAR_WALSH (which builds the task set); otherwise CHW_ERR_INVALID_ARG.
  *
- * chw_forward_haar -- y = H_m x together with its Haar side output z = Psi_m x: the CHW
- * algorithm run as its two parts, stage 0 (chw_haar into z) and stages 1..m-1
- * (chw_from_haar from z into y).  z must not overlap x or y.  Needs CHW_FLAG_HAAR_WALSH.
+ * chw_forward_haar -- y = H_m x together with its Haar side output z = Psi_m x (stage 0 of
+ * Theorem 1, "for free" from the cascade): y is bit for bit chw_forward's result and z
+ * chw_haar's, in every normalisation.  Where the plan's tier holds whole signals on one SM
+ * (single-CTA tiles, m <= 14; the tensor-memory tier, m = 15, 16; dyadic order) the
+ * kernels capture z from the same pass -- each detail right after the butterfly of its level, the approximation at
+ * the end -- so x is read once and y and z written once; other tiers run chw_haar and then
+ * the forward transform.  z must not overlap x or y (x == y is allowed).
  */
 chw_status_t chw_from_haar(chw_plan_t plan, const void* z, void* y, void* stream);
 chw_status_t chw_forward_haar(chw_plan_t plan, const void* x, void* y, void* z, void* stream);
@@ -257,25 +291,36 @@ chw_status_t chw_forward_host(chw_plan_t plan, const void* x_host, void* y_host,
 /*
  * chw_forward_noalloc -- y = H_m x for `batch` signals through the two-HBM-pass kernels,
  * without allocating anything.  (The paper has no counterpart; this is a library entry
- * point for callers that cannot allocate device memory when they transform: work being
- * captured into a CUDA graph, where cudaMalloc is not allowed; processes whose device
- * memory belongs to another allocator; and latency-critical code that cannot take
- * cudaMalloc's implicit synchronisation.)
- *   m, batch, dtype, norm  as for chw_plan, restricted to 18 <= m <= 22, CHW_F32 or
- *          CHW_I32, and batch * 2^m <= 2^22 elements: the pass-1 intermediate lives in
- *          a fixed 16 MiB device array of the library, which every GPU that loads the
- *          library holds until the process exits.  Larger requests return
- *          CHW_ERR_INVALID_ARG.
+ * point for callers that cannot allocate device memory when they transform: processes
+ * whose device memory has been handed in full to another allocator, such as a caching
+ * pool that reserved it all; latency-critical code that cannot take cudaMalloc's implicit
+ * device-wide synchronisation; and code running where the CUDA runtime's allocator may
+ * not be called.)
+ *   m, batch, dtype, norm  as for chw_plan.  m outside 18..22 and dtypes other than
+ *          CHW_F32 / CHW_I32 return CHW_ERR_UNSUPPORTED; batch * 2^m above 2^22 elements
+ *          returns CHW_ERR_INVALID_ARG: the pass-1 intermediate lives in a fixed 16 MiB
+ *          device array of the library, which every GPU that loads the library holds
+ *          until the process exits.
  *   x, y   device buffers as for chw_forward (16-byte aligned); stream as elsewhere.
- * No plan object, no cudaMalloc/cudaFree.  The first call on a device looks up the
- * array's device address (once per device, with that device current); make that first
- * call before any stream capture.  All calls share the array, which keeps the previous
- * call's contents: calls whose work overlaps on the GPU (different streams, or devices
- * sharing no order) race on it and must be serialised by the caller.  Bounded-wait
- * timeouts are recorded in the array's header word, which each call clears first.
+ * It launches exactly what chw_forward does for a two-pass plan of the same shape (same
+ * split, same kernels, bit-identical results).  No plan object, no cudaMalloc/cudaFree.
+ * The first call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  All calls share
+ * the array, which keeps the previous call's contents: calls whose work overlaps on the
+ * GPU (different streams, or devices sharing no order) race on it and must be serialised
+ * by the caller.  A bounded device wait that gives up latches CHW_ERR_TIMEOUT into the
+ * array's header word, which each call clears first; read it with
+ * chw_noalloc_device_status().
  */
 chw_status_t chw_forward_noalloc(int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm, const void* x, void* y,
                                  void* stream);
+
+/*
+ * chw_noalloc_device_status -- the device-side status of chw_forward_noalloc on the current
+ * device: synchronises the device, returns the error latched by the calls since the last
+ * read (CHW_ERR_TIMEOUT) or CHW_OK, and clears it.  Allocates nothing.
+ */
+chw_status_t chw_noalloc_device_status(void);
 
 /* Fill *info with what the plan launches. */
 chw_status_t chw_plan_get_info(chw_plan_t plan, chw_plan_info_t* info);
@@ -315,6 +360,8 @@ void chw_tune_cache_clear(void);
  * chw_last_device_status -- synchronise the plan's device work and report the first
  * device-side error latched since the previous call (CHW_ERR_TIMEOUT,
  * CHW_ERR_DEVICE_CHECK) or an asynchronous CUDA error (CHW_ERR_CUDA); clears the latch.
+ * For CHW_ERR_DEVICE_CHECK, chw_last_error_message() names the first offending element
+ * index.
  */
 chw_status_t chw_last_device_status(chw_plan_t plan);
 

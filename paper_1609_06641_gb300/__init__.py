@@ -21,11 +21,13 @@ from ._lib import (
     CHW_F16,
     CHW_F32,
     CHW_FLAG_AUTOTUNE,
+    CHW_FLAG_CHECKED,
     CHW_FLAG_CLUSTER,
     CHW_FLAG_HAAR_WALSH,
     CHW_FLAG_ORDER_NATURAL,
     CHW_FLAG_ORDER_SEQUENCY,
     CHW_FLAG_ROWSTACK,
+    CHW_FLAG_TEST_CORRUPT,
     CHW_FLAG_TEST_STALL,
     CHW_FLAG_FORCE_MULTIPASS,
     CHW_FLAG_FORCE_SIMPLE,
@@ -134,8 +136,12 @@ def chw_plan(m, batch, dtype="f32", norm="end", flags=CHW_FLAG_NONE, order="dyad
     return Plan(h, int(m), int(batch), d, nm)
 
 
-def chw_plan_ragged(ms, dtype="f32", norm="end", flags=CHW_FLAG_NONE):
-    """Plan one persistent launch over signals of lengths 2^ms[i] (see chw_plan_ragged)."""
+def chw_plan_ragged(ms, dtype="f32", norm="end", flags=CHW_FLAG_NONE, offsets=None, total=None):
+    """Plan one graph launch over signals of lengths 2^ms[i] (see chw_plan_ragged).
+
+    With ``offsets`` (one element offset per signal) and ``total`` (elements of x and y) the
+    signals sit where the caller put them (chw_plan_ragged_at); otherwise the library packs
+    them (chw_ragged_offsets)."""
     import numpy as np
 
     lib = _lib.load()
@@ -143,10 +149,20 @@ def chw_plan_ragged(ms, dtype="f32", norm="end", flags=CHW_FLAG_NONE):
     h = ctypes.c_void_p()
     d = _code(dtype, DTYPES, "dtype")
     nm = _code(norm, NORMS, "norm")
-    _lib.check(
-        lib.chw_plan_ragged(ctypes.byref(h), arr.ctypes.data_as(ctypes.c_void_p), arr.size, d, nm, int(flags)),
-        "chw_plan_ragged",
-    )
+    if offsets is None:
+        _lib.check(
+            lib.chw_plan_ragged(ctypes.byref(h), arr.ctypes.data_as(ctypes.c_void_p), arr.size, d, nm, int(flags)),
+            "chw_plan_ragged",
+        )
+    else:
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        if off.size != arr.size or total is None:
+            raise ValueError("offsets needs one entry per signal, and total")
+        _lib.check(
+            lib.chw_plan_ragged_at(ctypes.byref(h), arr.ctypes.data_as(ctypes.c_void_p),
+                                   off.ctypes.data_as(ctypes.c_void_p), arr.size, int(total), d, nm, int(flags)),
+            "chw_plan_ragged_at",
+        )
     return Plan(h, -1, int(arr.size), d, nm, ragged_ms=arr)
 
 

@@ -37,6 +37,8 @@ CHW_FLAG_ORDER_SEQUENCY = 32
 CHW_FLAG_TEST_STALL = 64
 CHW_FLAG_CLUSTER = 128
 CHW_FLAG_AUTOTUNE = 256
+CHW_FLAG_CHECKED = 512
+CHW_FLAG_TEST_CORRUPT = 1024
 
 
 class chw_plan_info_t(ctypes.Structure):
@@ -67,6 +69,10 @@ _P = ctypes.c_void_p
 _SIGNATURES = {
     "chw_plan": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32]),
     "chw_plan_ragged": (ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32]),
+    "chw_plan_ragged_at": (
+        ctypes.c_int,
+        [ctypes.POINTER(_P), _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32],
+    ),
     "chw_ragged_offsets": (ctypes.c_int, [_P, _P]),
     "chw_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "chw_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -77,6 +83,7 @@ _SIGNATURES = {
     "chw_from_haar": (ctypes.c_int, [_P, _P, _P, _P]),
     "chw_forward_haar": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "chw_forward_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "chw_noalloc_device_status": (ctypes.c_int, []),
     "chw_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(chw_plan_info_t)]),
     "chw_last_device_status": (ctypes.c_int, [_P]),
     "chw_plan_destroy": (ctypes.c_int, [_P]),

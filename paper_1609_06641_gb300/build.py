@@ -89,6 +89,17 @@ def _inst(shape, var, extern):
     return f"{kw} cudaError_t chw::launch_fused<{tlo}, {m}, {tb}, {cb}, {bf}, {sc}, {om}>{SIG};\n"
 
 
+# Single-CTA dyadic row kernels that also write the Haar side output (fused.cuh, HZ): one
+# per m = 1..14, on the tile the plain kernel of that m uses.
+HZ_SHAPES = [(m, 13 if m <= 13 else 14) for m in range(1, 15)]
+
+
+def _inst_hz(m, tb, var, extern):
+    bf, sc = BF[var]
+    kw = "extern template" if extern else "template"
+    return f"{kw} cudaError_t chw::launch_fused<0, {m}, {tb}, 0, {bf}, {sc}, 0, true>{SIG};\n"
+
+
 def _generate():
     os.makedirs(GEN, exist_ok=True)
     files = {}
@@ -97,9 +108,13 @@ def _generate():
         name = f"fused_{tlo}_{m}_{tb}_{cb}_{om}.cu"
         body = '#include "launch.cuh"\n' + "".join(_inst(shape, v, False) for v in vars_)
         files[name] = body
+    for m, tb in HZ_SHAPES:
+        files[f"fused_hz_{m}_{tb}.cu"] = '#include "launch.cuh"\n' + "".join(_inst_hz(m, tb, v, False) for v in ALL)
     lk = ['#include "launch.cuh"\n']
     for shape in SHAPES:
         lk += [_inst(shape, v, True) for v in shape[5]]
+    for m, tb in HZ_SHAPES:
+        lk += [_inst_hz(m, tb, v, True) for v in ALL]
     lk.append("namespace chw {\nFusedLaunchFn lookup_fused(int tlo, int m, int tb, int cb, int var, int om) {\n")
     for shape in SHAPES:
         tlo, m, tb, cb, om, vars_ = shape
@@ -107,6 +122,14 @@ def _generate():
         for v in vars_:
             bf, sc = BF[v]
             lk.append(f"    if (var == {v}) return &launch_fused<{tlo}, {m}, {tb}, {cb}, {bf}, {sc}, {om}>;\n")
+        lk.append("    return nullptr;\n  }\n")
+    lk.append("  return nullptr;\n}\n")
+    lk.append("FusedLaunchFn lookup_fused_hz(int m, int tb, int var) {\n")
+    for m, tb in HZ_SHAPES:
+        lk.append(f"  if (m == {m} && tb == {tb}) {{\n")
+        for v in ALL:
+            bf, sc = BF[v]
+            lk.append(f"    if (var == {v}) return &launch_fused<0, {m}, {tb}, 0, {bf}, {sc}, 0, true>;\n")
         lk.append("    return nullptr;\n  }\n")
     lk.append("  return nullptr;\n}\n}  // namespace chw\n")
     files["fused_lookup.cu"] = "".join(lk)
@@ -147,7 +170,7 @@ def _digest():
 # benchmark's roofline record names); their digest (code only, comments removed) is
 # recorded next to committed DRAM-traffic figures so that a figure is used only while the
 # code it was measured on is unchanged.
-KERNEL_SOURCES = ("ptx.cuh", "engine.cuh", "fused.cuh", "launch.cuh", "tmem.cuh", "tmem.cu")
+KERNEL_SOURCES = ("ptx.cuh", "engine.cuh", "fused.cuh", "launch.cuh", "tmem.cuh", "tmem_launch.cuh", "tmem.cu")
 
 
 def _code_only(text):

@@ -21,7 +21,7 @@
 #include "tune.h"
 
 namespace chw {
-using LowpLaunchFn = cudaError_t (*)(const CUtensorMap*, const LowpArgs&, int64_t, cudaStream_t);
+using LowpLaunchFn = cudaError_t (*)(const CUtensorMap*, const CUtensorMap*, const LowpArgs&, int64_t, cudaStream_t);
 LowpLaunchFn lookup_lowp(int m, bool f16, bool end);
 using RowstackLaunchFn = cudaError_t (*)(const CUtensorMap*, const FusedArgs&, uint32_t*, int64_t, int64_t,
                                          cudaStream_t);
@@ -77,22 +77,25 @@ int cluster_tile_bits() {
   return v;
 }
 
-// Column bits a of the two-pass split y = H_b X^T H_a for m = 18..29 (b = m - a row bits).
+// Column bits a of the two-pass split y = H_b X^T H_a for m = 18..30 (b = m - a row bits).
 // Measured on GB300 (fp32, 1 GiB per call): single-CTA tiles in both passes are fastest
 // up to m = 23 (a = 9); beyond, the first pass runs rows of 2^15 or 2^16 words on the
 // tensor-memory kernel, so b = m - a is kept at 15..16 with the column pass as small as
-// that allows: a = max(9, m - 16), at most 12 (m = 24..28: 2939, 2875, 2371, 2260, 1824
-// GB/s against 2414, -, 1900, -, 1500 for the earlier a = 11 splits).  CHW_TWO_PASS_A
-// (6..12, m - a in 5..17) overrides it (tuning).
-int two_pass_col_bits(int m) {
+// that allows: a = max(9, m - 16).  Column passes of a = 10..14 bits run on the
+// tensor-memory kernel as well (column blocks of 2^a rows x 2^min(5, 16-a) columns, at
+// most 2^16 words); the fused and cluster column kernels take a <= 12, so sequency order
+// (whose column pass they run) keeps a <= 12.  CHW_TWO_PASS_A (6..14, m - a in 5..17)
+// overrides it (tuning).
+int two_pass_col_bits(int m, int order = 0) {
   static const int v = [] {
     const char* e = std::getenv("CHW_TWO_PASS_A");
     return e ? std::atoi(e) : 0;
   }();
-  if (v >= 6 && v <= 12 && m - v <= 17 && m - v >= 5) return v;
+  const int amax = order == 2 ? 12 : 14;
+  if (v >= 6 && v <= amax && m - v <= 17 && m - v >= 5) return v;
   if (m <= 23) return 9;
   const int a = m - 16 > 9 ? m - 16 : 9;
-  return a < 12 ? a : 12;
+  return a < amax ? a : amax;
 }
 
 // One-pass row kernel shape for a transform of M bits; `tb` = preferred CTA tile bits for
@@ -171,6 +174,43 @@ chw_status_t make_runs_map(CUtensorMap* map, const void* ptr, int64_t total, int
   return CHW_OK;
 }
 
+// Sequency-order stores of the tensor-memory kernel: `total` words at `ptr` viewed in 3-D as
+// {2^run_bits words, run parity (2), run pair}; boxes of 32 words x 1 x 128 run pairs,
+// SWIZZLE_128B (one box holds 128 runs of one parity).
+chw_status_t make_seq_map(CUtensorMap* map, const void* ptr, int64_t total, int run_bits) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (total % (int64_t{256} << run_bits) != 0) return fail(CHW_ERR_INVALID_ARG, "internal: sequency runs");
+  cuuint64_t dims[3] = {cuuint64_t{1} << run_bits, 2, static_cast<cuuint64_t>(total >> (run_bits + 1))};
+  cuuint64_t strides[2] = {cuuint64_t{4} << run_bits, cuuint64_t{8} << run_bits};
+  cuuint32_t box[3] = {32, 1, 128};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void*>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CHW_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return CHW_OK;
+}
+
+// The column-blocked scratch of a two-pass split (rows of 2^M words, 2^a rows per signal,
+// blocks of 32 columns) as the 5-D view {32 words, row r, segment g mod 2^(M-13), run
+// g >> (M-13), signal}: element k of row r of signal s at s 2^(a+M) + (k >> 5) 2^(a+5) +
+// 32 r + (k & 31); boxes of 32 words x 1 x 1 x 256 runs x 1, SWIZZLE_128B (the
+// tensor-memory kernel's staged output chunks).  False if the driver rejects the view.
+bool make_colblock_map(CUtensorMap* map, const void* ptr, int64_t total, int M, int a) {
+  auto enc = tensor_map_encoder();
+  if (!enc || M < 13 || total % (int64_t{1} << (a + M)) != 0) return false;
+  const cuuint64_t w = 4;
+  cuuint64_t dims[5] = {32, cuuint64_t{1} << a, cuuint64_t{1} << (M - 13), 256,
+                        static_cast<cuuint64_t>(total >> (a + M))};
+  cuuint64_t strides[4] = {w * 32, w << (a + 5), w << (a + M - 8), w << (a + M)};
+  cuuint32_t box[5] = {32, 1, 1, 256, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 namespace chw {
@@ -219,6 +259,8 @@ struct chw_plan_s {
   chw::RaggedPlan* hw = nullptr;  // only for tiny totals that are not whole 32-word rows
   bool hw_ready = false;
   chw_plan_s* hw_big[CHW_MAX_M] = {};
+  // chw_forward_haar: the Haar side output of the current call (fused tiers only), else null
+  void* call_haar_z = nullptr;
 };
 
 namespace {
@@ -238,6 +280,15 @@ int final_outmode(const chw_plan_s* p) {
   if (p->m <= 1) return 0;
   return p->order == 1 ? 2 : (p->order == 2 ? 3 : 0);
 }
+
+// Checked mode (CHW_FLAG_CHECKED): the launch range-checks its indices against these bounds.
+void set_checks(chw::FusedArgs* a, const chw_plan_s* p, int64_t in_total) {
+  a->checked = (p->flags & CHW_FLAG_CHECKED) != 0;
+  a->in_total = in_total;
+}
+
+// Device status block of a plan: int code, int (unused), int64 first offending index.
+constexpr size_t kStatusBytes = 16;
 
 chw_status_t validate_data_ptr(const void* p, const char* name) {
   if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "%s is NULL", name);
@@ -265,20 +316,35 @@ void enable_tile_store(chw::FusedArgs* a, void* out, int64_t total, int tlo, int
 chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
                                int64_t units, int64_t ustride, int64_t ubase, const int8_t* diag_in,
                                const int8_t* diag_out, float scale, cudaStream_t st, int colblock_a = 0,
-                               int64_t diag_mask = 0);
+                               int64_t diag_mask = 0, int colblock_c = 0);
 
 // The first pass of a two-pass split takes the tensor-memory kernel for rows of 2^15 and
 // 2^16 words (unless the plan asks for 2^13-word cluster tiles).
-bool tmem_row_pass(const chw_plan_s* p, int M, int om) { return om == 1 && (M == 15 || M == 16) && p->tile_bits != 13; }
+bool tmem_row_pass_tb(int tile_bits, int M, int om) { return om == 1 && (M == 15 || M == 16) && tile_bits != 13; }
+bool tmem_row_pass(const chw_plan_s* p, int M, int om) { return tmem_row_pass_tb(p->tile_bits, M, om); }
+
+// log2 of the columns per block of a tensor-memory column pass of A row bits after a first
+// pass of B bits (dyadic output), or 0 when the fused / cluster column kernels run it:
+// column blocks of 2^A x 32 for A = 10, 11 (2^15, 2^16 words), and narrower blocks of
+// 2^(16 - A) columns for A = 12..14, which only the tensor-memory first pass can write.
+int tmem_col_bits_tb(int tile_bits, int A, int B, int om) {
+  if (om != 0 || A < 10 || A > 14 || tile_bits == 13) return 0;
+  if (A <= 11) return 5;
+  return tmem_row_pass_tb(tile_bits, B, 1) ? 16 - A : 0;
+}
+int tmem_col_bits(const chw_plan_s* p, int A, int B, int om) { return tmem_col_bits_tb(p->tile_bits, A, B, om); }
 
 chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
                              const int8_t* diag_in, const int8_t* diag_out, int64_t diag_mask, int colblock_a,
-                             float scale, cudaStream_t st) {
+                             float scale, cudaStream_t st, int colblock_c = 0) {
   if (tmem_row_pass(p, M, om) && diag_out == nullptr)
     return launch_tmem_units(p, M, 1, var, in, out, total, total >> M, 0, 0, diag_in, nullptr, scale, st, colblock_a,
-                             diag_mask);
+                             diag_mask, colblock_c);
+  if (colblock_c != 0 && colblock_c != 5)
+    return fail(CHW_ERR_UNSUPPORTED, "internal: column blocks narrower than 32 need the tensor-memory first pass");
   const Shape s = row_shape(M, p->tile_bits);
-  chw::FusedLaunchFn fn = chw::lookup_fused(0, M, s.tb, s.cb, var, om);
+  const bool hz = p->call_haar_z != nullptr && om == 0 && s.cb == 0;  // chw_forward_haar
+  chw::FusedLaunchFn fn = hz ? chw::lookup_fused_hz(M, s.tb, var) : chw::lookup_fused(0, M, s.tb, s.cb, var, om);
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no row kernel for M=%d tb=%d cb=%d out=%d", M, s.tb, s.cb, om);
   CUtensorMap map;
   chw_status_t r = make_rows_map(&map, in, total, s.tb);
@@ -291,9 +357,11 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
   a.diag_out = diag_out;
   a.diag_mask = diag_mask;
   a.status = p->d_status;
+  set_checks(&a, p, total);
   a.colblock_a = colblock_a;
   a.order_m = M;
   a.nat_b = 0;
+  a.haar_z = p->call_haar_z;  // (used by whole-signal row tiles in a final order only)
   a.stall_cta = (p->flags & CHW_FLAG_TEST_STALL) != 0 ? 2 : 0;  // rank 1 withholds its signal
   a.wait_tries = (p->flags & CHW_FLAG_TEST_STALL) != 0 ? 4096u : 0u;
   if (s.cb == 0) enable_tile_store(&a, out, total, 0, M, s.tb, om);
@@ -308,14 +376,24 @@ chw_status_t launch_row_pass(chw_plan_s* p, int M, int om, int var, const void* 
 chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void* in, void* out, int64_t total,
                                int64_t units, int64_t ustride, int64_t ubase, const int8_t* diag_in,
                                const int8_t* diag_out, float scale, cudaStream_t st, int colblock_a,
-                               int64_t diag_mask) {
-  chw::TmemLaunchFn fn = chw::lookup_tmem(M, var, om);
+                               int64_t diag_mask, int colblock_c) {
+  const bool hz = p->call_haar_z != nullptr && om == 0;  // chw_forward_haar
+  chw::TmemLaunchFn fn = hz ? chw::lookup_tmem_hz(M, var) : chw::lookup_tmem(M, var, om);
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no tensor-memory kernel for m=%d out=%d", M, om);
   CUtensorMap map, omap;
   chw_status_t r = make_rows_map(&map, in, total, 14);
   if (r != CHW_OK) return r;
-  // (sequency order stores through the SM; its kernel does not read the map)
-  r = om == 2 ? make_runs_map(&omap, out, total, M - 6, 64) : make_runs_map(&omap, out, total, M - 8, 256);
+  bool cb_tma = false;  // the column-blocked first pass by tensor stores (blocks of 32 columns)
+  if (om == 2) {
+    r = make_runs_map(&omap, out, total, M - 6, 64);
+  } else if (om == 3) {
+    r = make_seq_map(&omap, out, total, M - 8);
+  } else if (om == 1) {
+    r = CHW_OK;
+    if (colblock_c == 0 || colblock_c == 5) cb_tma = make_colblock_map(&omap, out, total, M, colblock_a);
+  } else {
+    r = make_runs_map(&omap, out, total, M - 8, 256);
+  }
   if (r != CHW_OK) return r;
   chw::FusedArgs a{};
   a.out = out;
@@ -325,10 +403,38 @@ chw_status_t launch_tmem_units(chw_plan_s* p, int M, int om, int var, const void
   a.diag_out = diag_out;
   a.diag_mask = diag_mask != 0 ? diag_mask : (int64_t{1} << M) - 1;
   a.status = p->d_status;
+  set_checks(&a, p, total);
   a.unit_stride = ustride;
   a.unit_base = ubase;
   a.colblock_a = colblock_a;
+  a.colblock_c = colblock_c;
+  a.tma_store = cb_tma ? 1 : 0;
+  a.haar_z = p->call_haar_z;  // (used by whole signals in a final order only)
   CHW_CUDA(fn(&map, &omap, a, units, st));
+  return CHW_OK;
+}
+
+// Second pass of a two-pass split on the tensor-memory kernel: column blocks of 2^A rows x
+// 2^clo columns (2^(A+clo) words each, back to back in `in`), output rows contiguous.
+chw_status_t launch_tmem_col_pass(chw_plan_s* p, int A, int clo, int var, const void* in, void* out, int64_t total,
+                                  const int8_t* diag_out, int64_t diag_mask, float scale, cudaStream_t st) {
+  const int M = A + clo;
+  chw::TmemLaunchFn fn = chw::lookup_tmem_col(M, clo, var);
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no tensor-memory column kernel for A=%d", A);
+  CUtensorMap map, omap;
+  chw_status_t r = make_rows_map(&map, in, total, 14);
+  if (r != CHW_OK) return r;
+  r = make_runs_map(&omap, out, total, M - 8, 256);
+  if (r != CHW_OK) return r;
+  chw::FusedArgs a{};
+  a.out = out;
+  a.out_total = total;
+  a.end_scale = scale;
+  a.diag_out = diag_out;
+  a.diag_mask = diag_mask;
+  a.status = p->d_status;
+  set_checks(&a, p, total);
+  CHW_CUDA(fn(&map, &omap, a, total >> M, st));
   return CHW_OK;
 }
 
@@ -355,6 +461,7 @@ chw_status_t launch_col_pass(chw_plan_s* p, int A, int var, int om, const void* 
   a.diag_out = diag_out;
   a.diag_mask = diag_mask;
   a.status = p->d_status;
+  set_checks(&a, p, total);
   a.colblock_a = 0;
   a.order_m = p->m;
   a.nat_b = p->m - A;
@@ -384,8 +491,10 @@ chw_status_t launch_lowp_fused(chw_plan_s* p, const void* x, void* y, int64_t ba
                                int32_t* exp_out, const int8_t* diag_in, const int8_t* diag_out, cudaStream_t st) {
   chw::LowpLaunchFn fn = chw::lookup_lowp(p->m, p->dtype == CHW_F16, p->norm == CHW_NORM_END);
   if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no fused 16-bit kernel for m=%d", p->m);
-  CUtensorMap map;
+  CUtensorMap map, omap;
   chw_status_t r = make_codes_map(&map, x, batch, p->m);
+  if (r != CHW_OK) return r;
+  r = make_codes_map(&omap, y, batch, p->m);  // the one-warp kernel's output stores
   if (r != CHW_OK) return r;
   chw::LowpArgs a{};
   a.out = y;
@@ -394,8 +503,8 @@ chw_status_t launch_lowp_fused(chw_plan_s* p, const void* x, void* y, int64_t ba
   a.end_scale = end_scale_f32(p->m);
   a.diag_in = diag_in;
   a.diag_out = diag_out;
-  a.status = p->d_status;
-  CHW_CUDA(fn(&map, a, batch, st));
+  a.status = p->d_status;  // (the 16-bit kernel indexes by signal number only: no checks)
+  CHW_CUDA(fn(&map, &omap, a, batch, st));
   return CHW_OK;
 }
 
@@ -416,6 +525,7 @@ chw_status_t launch_rowstack(chw_plan_s* p, const void* x, void* y, int64_t batc
   a.diag_out = diag_out;
   a.diag_mask = (int64_t{1} << p->m) - 1;
   a.status = p->d_status;
+  set_checks(&a, p, total);
   const int64_t grid = batch < slots ? batch : slots;
   CHW_CUDA(fn(&map, a, static_cast<uint32_t*>(ws), grid, batch, st));
   return CHW_OK;
@@ -473,9 +583,13 @@ chw_status_t run_transform(chw_plan_s* p, const void* x, void* y, int64_t batch,
     case kTierTwoPass: {
       const int b = p->row_bits, a = m - b;
       const int om2 = final_outmode(p);
+      const int clo = tmem_col_bits(p, a, b, om2);
       chw_status_t r = launch_row_pass(p, b, om2 == 2 ? 4 : 1, fused_variant(p, false), x, ws, total, diag_in,
-                                       nullptr, dmask, a, 1.0f, st);
+                                       nullptr, dmask, a, 1.0f, st, clo);
       if (r != CHW_OK) return r;
+      if (clo != 0)
+        return launch_tmem_col_pass(p, a, clo, fused_variant(p, true), ws, y, total, diag_out, dmask,
+                                    end_scale_f32(m), st);
       return launch_col_pass(p, a, fused_variant(p, true), om2, ws, y, total, diag_out, dmask, end_scale_f32(m), st);
     }
     default:
@@ -532,7 +646,7 @@ chw_status_t build_haar_walsh(chw_plan_s* p) {
   std::string why;
   p->hw = chw::ragged_create_at(ms.data(), off.data(), static_cast<int64_t>(ms.size()), p->total,
                                 p->dtype == CHW_I32 ? chw::kVarI32 : fused_variant(p, true), p->d_status, false,
-                                &why);
+                                &why, (p->flags & CHW_FLAG_CHECKED) != 0);
   if (p->hw == nullptr) return fail(CHW_ERR_CUDA, "Haar-Walsh task set: %s", why.c_str());
   for (int k = chw::kRaggedMaxM + 1; k < m; ++k) {
     chw_status_t r = chw_plan(&p->hw_big[k], k, 1, p->dtype, p->norm, 0);
@@ -558,6 +672,7 @@ chw_status_t launch_units(chw_plan_s* p, int M, int om, int var, const void* in,
   a.end_scale = scale;
   a.diag_mask = (int64_t{1} << p->m) - 1;
   a.status = p->d_status;
+  set_checks(&a, p, total);
   a.order_m = M;
   a.head_end = head_end;
   a.unit_stride = ustride;
@@ -605,9 +720,12 @@ chw_status_t run_haar_walsh(chw_plan_s* p, const void* z, void* y, cudaStream_t 
 }
 
 // Read and clear a device status word (after a device synchronisation).
-chw_status_t take_status(int* d_status, int* out) {
-  CHW_CUDA(cudaMemcpy(out, d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  CHW_CUDA(cudaMemset(d_status, 0, sizeof(int)));
+chw_status_t take_status(int* d_status, int* out, int64_t* index = nullptr) {
+  int32_t block[4] = {};
+  CHW_CUDA(cudaMemcpy(block, d_status, kStatusBytes, cudaMemcpyDeviceToHost));
+  CHW_CUDA(cudaMemset(d_status, 0, kStatusBytes));
+  *out = block[0];
+  if (index != nullptr) std::memcpy(index, block + 2, sizeof(int64_t));
   return CHW_OK;
 }
 
@@ -654,7 +772,7 @@ std::vector<chw::TuneChoice> tune_candidates(int m, chw_dtype_t dtype, chw_norm_
   std::vector<chw::TuneChoice> c;
   const uint32_t fixed = CHW_FLAG_FORCE_SIMPLE | CHW_FLAG_FORCE_MULTIPASS | CHW_FLAG_ROWSTACK | CHW_FLAG_CLUSTER |
                          CHW_FLAG_TEST_STALL;
-  if (is_lowp(dtype) || (flags & fixed) != 0 || m < 14 || m > 29) return c;
+  if (is_lowp(dtype) || (flags & fixed) != 0 || m < 14 || m > CHW_MAX_M) return c;
   const int order = (flags & CHW_FLAG_ORDER_NATURAL) != 0 ? 1 : ((flags & CHW_FLAG_ORDER_SEQUENCY) != 0 ? 2 : 0);
   const int om = m <= 1 ? 0 : (order == 1 ? 2 : (order == 2 ? 3 : 0));
   int var_last, var_first;
@@ -682,16 +800,19 @@ std::vector<chw::TuneChoice> tune_candidates(int m, chw_dtype_t dtype, chw_norm_
     if (om == 0 && m >= 15 && chw::lookup_rowstack(m, var_last) != nullptr) add(kTierRowStack, m, 14);
   }
   if (m >= 17) {
-    for (int a = 6; a <= 12; ++a) {
+    for (int a = 6; a <= 14; ++a) {
       const int b = m - a;
       if (b < 5 || b > 17) continue;
       for (int tb : {14, 13}) {
         const Shape s1 = row_shape(b, tb);
         const Shape s2 = om == 2 ? Shape{a <= 8 ? 13 : 14, 0} : col_shape(a, tb);
         const int om1 = om == 2 ? 4 : 1;
-        if (chw::lookup_fused(0, b, s1.tb, s1.cb, var_first, om1) == nullptr ||
-            chw::lookup_fused(5, a, s2.tb, s2.cb, var_last, om) == nullptr)
-          continue;
+        const int clo = tmem_col_bits_tb(tb, a, b, om);
+        const bool row_ok = tmem_row_pass_tb(tb, b, om1) ? chw::lookup_tmem(b, var_first, 1) != nullptr
+                                                        : chw::lookup_fused(0, b, s1.tb, s1.cb, var_first, om1) != nullptr;
+        const bool col_ok = clo != 0 ? chw::lookup_tmem_col(a + clo, clo, var_last) != nullptr
+                                     : chw::lookup_fused(5, a, s2.tb, s2.cb, var_last, om) != nullptr;
+        if (!row_ok || !col_ok) continue;
         const bool same = row_shape(b, 13).tb == row_shape(b, 14).tb && row_shape(b, 13).cb == row_shape(b, 14).cb &&
                           (om == 2 || (col_shape(a, 13).tb == col_shape(a, 14).tb && col_shape(a, 13).cb == col_shape(a, 14).cb));
         add(kTierTwoPass, b, same ? 14 : tb);
@@ -809,7 +930,7 @@ chw_status_t autotune_plan(chw_plan_s* p) {
     float ms = 0.f;
     int st = 0;
     cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaMemset(p->d_status, 0, sizeof(int));
+    cudaMemset(p->d_status, 0, kStatusBytes);
     if (!ok || st != 0 || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
       cudaGetLastError();
       continue;  // a candidate that fails is not chosen
@@ -832,6 +953,35 @@ chw_status_t autotune_plan(chw_plan_s* p) {
 }
 
 }  // namespace
+
+namespace chw {
+
+// Internal, for chw_forward_noalloc: the launches chw_forward makes for a two-pass plan of
+// this shape (the same split and kernels), with the pass-1 intermediate in caller-given
+// device memory `scratch` (batch * 2^m words) and device errors latched into `status`.
+// Allocates nothing: the plan descriptor lives on the host stack and only carries
+// arguments.
+chw_status_t two_pass_into(int m, int64_t batch, chw_dtype_t dtype, chw_norm_t norm, const void* x, void* y,
+                           void* scratch, int* status, cudaStream_t st) {
+  chw_plan_s t{};
+  CHW_CUDA(cudaGetDevice(&t.device));
+  t.m = m;
+  t.batch = batch;
+  t.dtype = dtype;
+  t.norm = norm;
+  t.total = batch << m;
+  t.tier = kTierTwoPass;
+  t.passes = 2;
+  t.row_bits = m - two_pass_col_bits(m);
+  t.d_status = status;
+  return run_transform(&t, x, y, batch, nullptr, nullptr, nullptr, nullptr, scratch, st);
+}
+
+// Internal: the reason chw_last_error_message() reports on this host thread.
+chw_status_t set_error(chw_status_t s, const char* msg) { return fail(s, "%s", msg); }
+void clear_error() { g_err.clear(); }
+
+}  // namespace chw
 
 extern "C" {
 
@@ -858,6 +1008,7 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
   chw_status_t r = check_plan_args(m, batch, dtype, norm);
   if (r != CHW_OK) return r;
 
+  if ((flags & CHW_FLAG_TEST_CORRUPT) != 0) return fail(CHW_ERR_INVALID_ARG, "CHW_FLAG_TEST_CORRUPT is for ragged plans");
   auto* p = new chw_plan_s();
   p->m = m;
   p->batch = batch;
@@ -927,14 +1078,14 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     } else {
       p->tier = kTierFused;
     }
-  } else if (m <= 29) {
+  } else if (m <= 29 || (m == 30 && p->order == 0)) {
     p->tier = kTierTwoPass;
     p->passes = 2;
-    const int a = two_pass_col_bits(m);
+    const int a = two_pass_col_bits(m, p->order);
     p->row_bits = m - a;
   } else {
     delete p;
-    return fail(CHW_ERR_UNSUPPORTED, "m=%d needs three HBM passes, which this library does not implement", m);
+    return fail(CHW_ERR_UNSUPPORTED, "m=%d in sequency order needs three HBM passes, which this library does not implement", m);
   }
 
   cudaError_t e = cudaGetDevice(&p->device);
@@ -942,12 +1093,12 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     delete p;
     return fail(CHW_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   }
-  e = cudaMalloc(&p->d_status, sizeof(int));
+  e = cudaMalloc(&p->d_status, kStatusBytes);
   if (e != cudaSuccess) {
     delete p;
     return fail(CHW_ERR_CUDA, "cudaMalloc(status): %s", cudaGetErrorString(e));
   }
-  cudaMemset(p->d_status, 0, sizeof(int));
+  cudaMemset(p->d_status, 0, kStatusBytes);
   if (autotune_requested(flags)) {
     r = autotune_plan(p);
     if (r != CHW_OK) {
@@ -1204,15 +1355,23 @@ chw_status_t chw_last_device_status(chw_plan_t p) {
   if (p == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan is NULL");
   CHW_CUDA(cudaDeviceSynchronize());
   int s = 0;
-  chw_status_t r = take_status(p->d_status, &s);
+  int64_t index = 0;
+  chw_status_t r = take_status(p->d_status, &s, &index);
   if (r != CHW_OK) return r;
   for (chw_plan_s* b : p->hw_big) {
     if (b == nullptr) continue;
     int sb = 0;
-    r = take_status(b->d_status, &sb);
+    int64_t ib = 0;
+    r = take_status(b->d_status, &sb, &ib);
     if (r != CHW_OK) return r;
-    if (s == 0) s = sb;
+    if (s == 0) {
+      s = sb;
+      index = ib;
+    }
   }
+  if (s == CHW_ERR_DEVICE_CHECK)
+    return fail(CHW_ERR_DEVICE_CHECK, "device check failed: element index %lld out of range",
+                static_cast<long long>(index));
   if (s != 0) return fail(static_cast<chw_status_t>(s), "device reported %s", chw_status_string(static_cast<chw_status_t>(s)));
   return CHW_OK;
 }
@@ -1262,28 +1421,34 @@ chw_status_t chw_forward_haar(chw_plan_t p, const void* x, void* y, void* z, voi
   g_err.clear();
   chw_status_t r = check_haar_call(p, x, y, "x", "y");
   if (r != CHW_OK) return r;
-  if (p->hw == nullptr && !p->hw_ready) return fail(CHW_ERR_INVALID_ARG, "the plan was made without CHW_FLAG_HAAR_WALSH");
-  if (z == nullptr) return fail(CHW_ERR_INVALID_ARG, "z is NULL");
+  r = validate_data_ptr(z, "z");
+  if (r != CHW_OK) return r;
   const size_t bytes = static_cast<size_t>(p->total) * 4;
   if (overlaps(x, z, bytes) || overlaps(y, z, bytes)) return fail(CHW_ERR_INVALID_ARG, "z overlaps x or y");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // One HBM round trip where the tier's kernels capture stage 0 (single-CTA row tiles of
+  // whole signals, the tensor-memory tier): z leaves the same pass as y.
+  const bool fused = p->m >= 1 && p->order == 0 &&
+                     (p->tier == kTierTmem || (p->tier == kTierFused && row_shape(p->m, p->tile_bits).cb == 0));
+  if (fused) {
+    p->call_haar_z = z;
+    r = run_transform(p, x, y, p->batch, nullptr, nullptr, nullptr, nullptr, p->workspace, st);
+    p->call_haar_z = nullptr;
+    return r;
+  }
+  // Otherwise z first (x may be y), then y, by the plan's own kernels.
   r = chw_haar(p, x, z, stream);
   if (r != CHW_OK) return r;
-  return chw_from_haar(p, z, y, stream);
+  return run_transform(p, x, y, p->batch, nullptr, nullptr, nullptr, nullptr, p->workspace, st);
 }
 
-chw_status_t chw_plan_ragged(chw_plan_t* out, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,
-                             chw_norm_t norm, uint32_t flags) {
-  g_err.clear();
-  if (out == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan output pointer is NULL");
-  *out = nullptr;
-  if (ms_host == nullptr || count < 1) return fail(CHW_ERR_INVALID_ARG, "ms_host is NULL or count < 1");
-  if (dtype != CHW_F32 && dtype != CHW_I32) return fail(CHW_ERR_UNSUPPORTED, "ragged plans take int32 or fp32");
-  chw_status_t r = check_plan_args(0, 1, dtype, norm);
-  if (r != CHW_OK) return r;
-  for (int64_t i = 0; i < count; ++i)
-    if (ms_host[i] > chw::kRaggedMaxM)
-      return fail(CHW_ERR_INVALID_ARG, "ms[%lld]=%d outside 0..%d", static_cast<long long>(i), ms_host[i],
-                  chw::kRaggedMaxM);
+}  // extern "C"
+
+namespace {
+
+// A ragged plan over signals at `offsets` (count + 1 entries, the last one = total).
+chw_status_t make_ragged(chw_plan_t* out, const uint8_t* ms_host, const int64_t* offsets, int64_t count,
+                         chw_dtype_t dtype, chw_norm_t norm, uint32_t flags) {
   auto* p = new chw_plan_s();
   p->m = -1;
   p->batch = count;
@@ -1292,15 +1457,32 @@ chw_status_t chw_plan_ragged(chw_plan_t* out, const uint8_t* ms_host, int64_t co
   p->flags = flags;
   p->tier = kTierRagged;
   cudaError_t e = cudaGetDevice(&p->device);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, kStatusBytes);
   if (e != cudaSuccess) {
     delete p;
     return fail(CHW_ERR_CUDA, "ragged plan: %s", cudaGetErrorString(e));
   }
-  cudaMemset(p->d_status, 0, sizeof(int));
+  cudaMemset(p->d_status, 0, kStatusBytes);
+  std::vector<int64_t> off(offsets, offsets + count + 1);
+  if ((flags & CHW_FLAG_TEST_CORRUPT) != 0) {
+    // test hook (checked plans only): the first signal with m >= 13 and the first with
+    // m <= 12 get offsets past the end of x and y (32-aligned, so only the range is wrong)
+    const int64_t past = ((off[count] + (int64_t{1} << 20)) + 31) & ~int64_t{31};
+    bool big = false, small = false;
+    for (int64_t i = 0; i < count; ++i) {
+      if (!big && ms_host[i] >= 13) {
+        off[i] = past;
+        big = true;
+      } else if (!small && ms_host[i] <= 12) {
+        off[i] = past + (int64_t{1} << 21);
+        small = true;
+      }
+    }
+  }
   std::string why;
-  p->ragged = chw::ragged_create(ms_host, count, dtype == CHW_I32 ? chw::kVarI32 : fused_variant(p, true),
-                                 p->d_status, autotune_requested(flags), &why);
+  p->ragged = chw::ragged_create_at(ms_host, off.data(), count, off[count],
+                                    dtype == CHW_I32 ? chw::kVarI32 : fused_variant(p, true), p->d_status,
+                                    autotune_requested(flags), &why, (flags & CHW_FLAG_CHECKED) != 0);
   if (p->ragged != nullptr && chw::ragged_tuned(p->ragged)) p->tuned = 1;
   if (p->ragged == nullptr) {
     cudaFree(p->d_status);
@@ -1311,6 +1493,68 @@ chw_status_t chw_plan_ragged(chw_plan_t* out, const uint8_t* ms_host, int64_t co
   p->passes = chw::ragged_passes(p->ragged);
   *out = p;
   return CHW_OK;
+}
+
+chw_status_t check_ragged_args(chw_plan_t* out, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,
+                               chw_norm_t norm, uint32_t flags) {
+  if (out == nullptr) return fail(CHW_ERR_INVALID_ARG, "plan output pointer is NULL");
+  *out = nullptr;
+  if (ms_host == nullptr || count < 1) return fail(CHW_ERR_INVALID_ARG, "ms_host is NULL or count < 1");
+  if (count > (int64_t{1} << 31) - 1) return fail(CHW_ERR_INVALID_ARG, "count must be below 2^31");
+  if (dtype != CHW_F32 && dtype != CHW_I32) return fail(CHW_ERR_UNSUPPORTED, "ragged plans take int32 or fp32");
+  chw_status_t r = check_plan_args(0, 1, dtype, norm);
+  if (r != CHW_OK) return r;
+  if ((flags & CHW_FLAG_TEST_CORRUPT) != 0 && (flags & CHW_FLAG_CHECKED) == 0)
+    return fail(CHW_ERR_INVALID_ARG, "CHW_FLAG_TEST_CORRUPT runs only with CHW_FLAG_CHECKED");
+  for (int64_t i = 0; i < count; ++i)
+    if (ms_host[i] > chw::kRaggedMaxM)
+      return fail(CHW_ERR_INVALID_ARG, "ms[%lld]=%d outside 0..%d", static_cast<long long>(i), ms_host[i],
+                  chw::kRaggedMaxM);
+  return CHW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+chw_status_t chw_plan_ragged(chw_plan_t* out, const uint8_t* ms_host, int64_t count, chw_dtype_t dtype,
+                             chw_norm_t norm, uint32_t flags) {
+  g_err.clear();
+  chw_status_t r = check_ragged_args(out, ms_host, count, dtype, norm, flags);
+  if (r != CHW_OK) return r;
+  std::vector<int64_t> off(count + 1);
+  chw::ragged_pack(ms_host, count, off.data());
+  return make_ragged(out, ms_host, off.data(), count, dtype, norm, flags);
+}
+
+chw_status_t chw_plan_ragged_at(chw_plan_t* out, const uint8_t* ms_host, const int64_t* offsets_host, int64_t count,
+                                int64_t total, chw_dtype_t dtype, chw_norm_t norm, uint32_t flags) {
+  g_err.clear();
+  chw_status_t r = check_ragged_args(out, ms_host, count, dtype, norm, flags);
+  if (r != CHW_OK) return r;
+  if (offsets_host == nullptr) return fail(CHW_ERR_INVALID_ARG, "offsets_host is NULL");
+  if (total < 1 || total > (int64_t{1} << 40)) return fail(CHW_ERR_INVALID_ARG, "total outside 1..2^40");
+  std::vector<int64_t> order(count);
+  for (int64_t i = 0; i < count; ++i) {
+    const int64_t o = offsets_host[i], n = int64_t{1} << ms_host[i];
+    if (o < 0 || o > total - n)
+      return fail(CHW_ERR_INVALID_ARG, "signal %lld at [%lld, %lld) is not inside [0, %lld)", static_cast<long long>(i),
+                  static_cast<long long>(o), static_cast<long long>(o + n), static_cast<long long>(total));
+    if (ms_host[i] >= 13 && o % 32 != 0)
+      return fail(CHW_ERR_ALIGNMENT, "signal %lld (m=%d) must start on a 32-element boundary (offset %lld)",
+                  static_cast<long long>(i), ms_host[i], static_cast<long long>(o));
+    order[i] = i;
+  }
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return offsets_host[a] < offsets_host[b]; });
+  for (int64_t k = 1; k < count; ++k) {
+    const int64_t a = order[k - 1], b = order[k];
+    if (offsets_host[b] < offsets_host[a] + (int64_t{1} << ms_host[a]))
+      return fail(CHW_ERR_INVALID_ARG, "signals %lld and %lld overlap", static_cast<long long>(a),
+                  static_cast<long long>(b));
+  }
+  std::vector<int64_t> off(offsets_host, offsets_host + count);
+  off.push_back(total);
+  return make_ragged(out, ms_host, off.data(), count, dtype, norm, flags);
 }
 
 chw_status_t chw_ragged_offsets(chw_plan_t p, int64_t* offsets_host) {

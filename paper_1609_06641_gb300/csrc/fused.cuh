@@ -50,6 +50,8 @@ struct FusedArgs {
   int64_t diag_mask;         // index within a signal = element index & diag_mask
   int* status;               // device status word (first error wins)
   int colblock_a;            // OUTMODE 1, 4: rows per signal = 2^colblock_a
+  int colblock_c;            // tensor-memory rows of a first pass: 2^colblock_c columns per
+                             //   column block (0: 32, the fused kernels' only width)
   int order_m;               // OUTMODE 3: bits of a signal (sequency order is per signal)
   int nat_b;                 // OUTMODE 2, column tiles: the first pass's bits (row stride 2^b)
   int head_end;              // OUTMODE 6: scale scale k by fp32(2^{-k/2}) on output (END)
@@ -70,8 +72,30 @@ struct FusedArgs {
   // Output by TMA tensor stores (batched single-CTA tiles in dyadic order, outputs one
   // contiguous run per tile, no D): `tout` views the output as tile_store_map describes.
   int tma_store;
+  // Checked mode (CHW_FLAG_CHECKED): every computed global index is range-checked before
+  // it is used -- input rows against [0, in_total), output elements against
+  // [0, out_total) -- and a bad one latches CHW_ERR_DEVICE_CHECK with the index into the
+  // status words instead of being accessed (the access is skipped; the output is then
+  // undefined).
+  int checked;
+  int64_t in_total;  // elements of the input that may be read (checked mode)
+  // Haar side output (chw_forward_haar): z = Psi_m x (eq. (2)) of every signal, written
+  // from the same pass at the signal's place in this array (the layout of y); nullptr: none.
+  void* haar_z;
   CUtensorMap tout;  // the type carries the alignment TMA needs
 };
+
+// Checked mode: latch CHW_ERR_DEVICE_CHECK and the offending element index (the first one
+// wins; status[2..3] hold the index as an int64).
+__device__ __forceinline__ void check_fail(int* status, int64_t index) {
+  if (atomicCAS(status, 0, kStatusDeviceCheck) == 0)
+    atomicExch(reinterpret_cast<unsigned long long*>(status + 2), static_cast<unsigned long long>(index));
+}
+
+// Checked mode: elements [e0, e0 + n) lie inside [0, total).
+__device__ __forceinline__ bool range_ok(int64_t e0, int64_t n, int64_t total) {
+  return e0 >= 0 && e0 <= total - n;
+}
 
 // Element where unit u's input (or output) starts: from a per-signal offset table when
 // one is given, else from the unit stride.
@@ -424,6 +448,22 @@ __device__ __forceinline__ void tile_issue(const CUtensorMap* tin, int in_row0, 
   for (int j = 0; j < NBOX; ++j) tma_load_2d(buf + j * BOXR * 32, tin, bar, 0, in_row0 + j * BOXR, pol);
 }
 
+// tile_issue for a tile whose first input element is e0: in checked mode a tile that does
+// not start on a 32-element row inside [0, in_total) is not loaded -- the index is latched
+// and the barrier's phase completed by a plain arrival, so the waits still end (the tile
+// then holds stale data).  A tile may run past in_total: the tensor map reads zeros there
+// (the tail tile of a batch whose length is not a multiple of the tile).
+template <int TB>
+__device__ __forceinline__ void tile_issue_at(const CUtensorMap* tin, int64_t e0, uint32_t* buf, uint64_t* bar,
+                                              const FusedArgs& args) {
+  if (args.checked && (e0 < 0 || e0 >= args.in_total || (e0 & 31) != 0)) {
+    check_fail(args.status, e0);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    return;
+  }
+  tile_issue<TB>(tin, static_cast<int>(e0 >> 5), buf, bar);
+}
+
 // Copy the staged tile (output order, staging swizzle) to global memory with coalesced
 // 16-byte stores; `out_base` is the element index of the (cluster) tile's first output.
 template <int TLO, int M, int TB, int CB, class BF, int OUTMODE>
@@ -441,6 +481,9 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
   constexpr int NCH = 1 << (TB - 2);
   constexpr int S = F.stage_s;
   constexpr bool ROWS = tile_store_layout(OUTMODE, CB);
+  // the same loop with and without the checked mode's range checks, chosen once
+  auto loop = [&](auto checked_c) {
+  constexpr bool CHECKED = decltype(checked_c)::value;
 #pragma unroll 4
   for (int c = threadIdx.x; c < NCH; c += NT) {
     const uint32_t o = static_cast<uint32_t>(c) << 2;
@@ -479,7 +522,12 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
           pos = (int64_t{1} << (M - 1 - c)) | (qe >> (c + 1));
           if (args.head_end) e[t] = __float_as_uint(__fmul_rn(__uint_as_float(e[t]), end_scale_dev(M - 1 - c)));
         }
-        out[(og + t) - qe + pos] = e[t];
+        const int64_t at = (og + t) - qe + pos;
+        if (CHECKED && !range_ok(at, 1, args.out_total)) {
+          check_fail(args.status, at);
+          continue;
+        }
+        out[at] = e[t];
       }
       continue;
     } else {
@@ -495,6 +543,10 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
       g ^= g >> 16;
       addr = (og - p0) + (static_cast<int64_t>(g) << 2);
       q = (__popc(h) & 1) ? make_uint4(q.z, q.w, q.y, q.x) : make_uint4(q.x, q.y, q.w, q.z);
+    }
+    if (CHECKED && !range_ok(addr, 4, args.out_total)) {
+      check_fail(args.status, addr);
+      continue;
     }
     if (args.diag_out != nullptr) {
       const int8_t* d = args.diag_out;
@@ -513,24 +565,134 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
     }
     st_global_v4(out + addr, q.x, q.y, q.z, q.w);
   }
+  };
+  if (args.checked) {
+    loop(std::true_type{});
+  } else {
+    loop(std::false_type{});
+  }
 }
 
-// Phases 1 and 2 of a tile in `buf` (TMA complete): on return v holds phase 2's values and
-// no thread reads `buf` any more once the caller has synchronised.  Only for tiles that
-// have a third phase.
-// Butterflies of a phase; masked for the Haar-Walsh head when HM > 0.
-template <Phase P, int LO, int HI, int HM, class BF>
-__device__ __forceinline__ void bfly(uint32_t (&v)[64], const BF& bf, uint32_t lane, uint32_t warp) {
+// ------------------------------------------------------------------ Haar side output
+// Stage 0 of Theorem 1 is the Haar transform Psi_m of eq. (2), and its levels are the
+// cascade's butterflies restricted to labels whose lower bits are zero: right after the
+// butterfly on label bit t, the label L with bits 0..t-1 zero and bit t one holds its
+// level-(t+1) detail, which eq. (2) places at z[2^(m-t-1) + (L >> (t+1))]; after the last
+// bit, label 0 holds the approximation z[0].  So z leaves the same pass as y, from the
+// registers, bit-identical to chw_haar (END: each coefficient multiplied once by
+// fp32(2^(-L/2)), L the levels behind it).
+struct HaarZ {
+  uint32_t* z;     // z element of the tile's label 0 (nullptr: no side output)
+  uint32_t hi;     // label bits of the tile above its own (tensor-memory rows), else 0
+  uint32_t limit;  // z elements of the tile that belong to its signals (tail tiles)
+};
+
+// fp32(2^(-L/2)), exactly as end_scale_dev forms it.
+constexpr float end_scale_const(int L) {
+  float r = (L & 1) ? 0.70710678118654752440f : 1.0f;
+  for (int i = 0; i < L / 2; ++i) r *= 0.5f;
+  return r;
+}
+
+// Register k of phase P holds a label captured after bit T (T == ZM: the approximation).
+template <int T, int ZM>
+constexpr bool z_hit(const Phase& p, int k) {
+  const uint32_t rl = reg_label(p, k), smask = (1u << ZM) - 1u;
+  return T < ZM ? (rl & ((2u << T) - 1u)) == (1u << T) : (rl & smask) == 0u;
+}
+// Its z position within the tile, less the thread's part.
+template <int T, int ZM>
+constexpr uint32_t z_rpart(const Phase& p, int k) {
+  const uint32_t rl = reg_label(p, k), smask = (1u << ZM) - 1u;
+  return ((rl >> ZM) << ZM) + (T < ZM ? (1u << (ZM - T - 1)) + ((rl & smask) >> (T + 1)) : 0u);
+}
+// The register holding the captured label at z position `at` (less the thread's part), or -1.
+template <int T, int ZM>
+constexpr int z_reg_at(const Phase& p, uint32_t at) {
+  for (int k = 0; k < (1 << p.nreg); ++k)
+    if (z_hit<T, ZM>(p, k) && z_rpart<T, ZM>(p, k) == at) return k;
+  return -1;
+}
+// The thread's part of a z position is a multiple of 4 (no thread-owned label bit lands on
+// its two low bits), so four consecutive register positions can leave as one 16-byte store.
+template <int T, int ZM>
+constexpr bool z_v4_ok(const Phase& p) {
+  if (T >= ZM) return false;
+  uint32_t tb = 0;
+  for (int i = 0; i < 5; ++i) tb |= 1u << p.lane[i];
+  for (int i = 0; i < p.nwarp; ++i) tb |= 1u << p.warp[i];
+  for (int i = 0; i < p.ncta; ++i) tb |= 1u << p.cta[i];
+  return ((tb >> (T + 1)) & 3u) == 0u && ZM - T - 1 >= 2;
+}
+
+// The captures after the butterflies of label bit T (T == ZM: the approximation, after the
+// last bit) for signals of 2^ZM labels; tl = the thread's label bits (with hz.hi).  Four
+// captures at consecutive z positions leave as one 16-byte store where the layout allows.
+template <Phase P, int T, int ZM, bool ZEND>
+__device__ __forceinline__ void haar_capture(const uint32_t (&v)[64], uint32_t tl, const HaarZ& hz) {
+  constexpr uint32_t smask = (1u << ZM) - 1u;
+  constexpr uint32_t below = T < ZM ? (1u << T) - 1u : smask;  // label bits that must be zero
+  if ((tl & below) != 0u) return;
+  const uint32_t tpart = ((tl >> ZM) << ZM) + (T < ZM ? ((tl & smask) >> (T + 1)) : 0u);
+  constexpr float sc = end_scale_const(T < ZM ? T + 1 : ZM);
+  constexpr bool V4 = z_v4_ok<T, ZM>(P);
+  auto scaled = [&](uint32_t x) {
+    if constexpr (ZEND) x = __float_as_uint(__fmul_rn(__uint_as_float(x), sc));
+    return x;
+  };
+  sfor<64>([&](auto kk) {
+    constexpr int k = kk;
+    if constexpr (z_hit<T, ZM>(P, k)) {
+      constexpr uint32_t rp = z_rpart<T, ZM>(P, k);
+      constexpr int k1 = z_reg_at<T, ZM>(P, rp | 1u), k2 = z_reg_at<T, ZM>(P, rp | 2u),
+                    k3 = z_reg_at<T, ZM>(P, rp | 3u);
+      constexpr bool group = V4 && (rp & 3u) == 0u && k1 >= 0 && k2 >= 0 && k3 >= 0;
+      constexpr bool member = V4 && (rp & 3u) != 0u && z_reg_at<T, ZM>(P, rp & ~3u) >= 0 &&
+                              z_reg_at<T, ZM>(P, (rp & ~3u) | 1u) >= 0 && z_reg_at<T, ZM>(P, (rp & ~3u) | 2u) >= 0 &&
+                              z_reg_at<T, ZM>(P, (rp & ~3u) | 3u) >= 0;
+      const uint32_t at = tpart + rp;
+      if constexpr (group) {
+        if (at + 3u < hz.limit)
+          st_global_v4(hz.z + at, scaled(v[k]), scaled(v[k1]), scaled(v[k2]), scaled(v[k3]));
+      } else if constexpr (!member) {
+        if (at < hz.limit) hz.z[at] = scaled(v[k]);
+      }
+    }
+  });
+}
+
+// Butterflies of a phase; masked for the Haar-Walsh head when HM > 0; with the Haar side
+// output captured bit by bit when ZM > 0 and hz names an output.
+template <Phase P, int LO, int HI, int HM, class BF, int ZM = 0, bool ZEND = false>
+__device__ __forceinline__ void bfly(uint32_t (&v)[64], const BF& bf, uint32_t lane, uint32_t warp,
+                                     const HaarZ* hz = nullptr) {
   if constexpr (HM > 0) {
     butterflies_head<P, LO, HI, HM>(v, bf, thread_label<P>(lane, warp, 0));
+  } else if constexpr (ZM > 0) {
+    if (hz == nullptr || hz->z == nullptr) {
+      butterflies<P, LO, HI>(v, bf);
+      return;
+    }
+    const uint32_t tl = thread_label<P>(lane, warp, 0) | hz->hi;
+    sfor<kMaxBits>([&](auto bb) {
+      constexpr int b = bb;
+      if constexpr (b >= LO && b < HI) {
+        butterflies<P, b, b + 1>(v, bf);
+        if constexpr (b < ZM) haar_capture<P, b, ZM, ZEND>(v, tl, *hz);
+        if constexpr (b == ZM - 1) haar_capture<P, ZM, ZM, ZEND>(v, tl, *hz);
+      }
+    });
   } else {
     butterflies<P, LO, HI>(v, bf);
   }
 }
 
-template <int TLO, int M, int TB, int CB, class BF, int HM = 0>
+// Phases 1 and 2 of a tile in `buf` (TMA complete): on return v holds phase 2's values and
+// no thread reads `buf` any more once the caller has synchronised.  Only for tiles that
+// have a third phase.  ZM, ZEND, hz: the Haar side output (see bfly).
+template <int TLO, int M, int TB, int CB, class BF, int HM = 0, int ZM = 0, bool ZEND = false>
 __device__ __forceinline__ void phases_1_2(uint32_t (&v)[64], int64_t in_elem0, const FusedArgs& args, uint32_t* buf,
-                                           const BF& bf) {
+                                           const BF& bf, const HaarZ* hz = nullptr) {
   using Cfg = FusedCfg<TLO, M, TB, CB>;
   constexpr FusedPlan F = Cfg::plan;
   static_assert(F.has_p3, "tiles with a third phase");
@@ -549,12 +711,12 @@ __device__ __forceinline__ void phases_1_2(uint32_t (&v)[64], int64_t in_elem0, 
         if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
       });
     }
-    bfly<P1, 0, 5, HM>(v, bf, lane, warp);
+    bfly<P1, 0, 5, HM, BF, ZM, ZEND>(v, bf, lane, warp, hz);
     store_phase<P1, P1, LS, LMASK>(v, buf, base);
     __syncthreads();
   }
   load_phase<P2, LS, LMASK>(v, buf, thread_pos<P2, LS, LMASK>(lane, warp, 0));
-  bfly<P2, (TLO > 5 ? TLO : 5), 11, HM>(v, bf, lane, warp);
+  bfly<P2, (TLO > 5 ? TLO : 5), 11, HM, BF, ZM, ZEND>(v, bf, lane, warp, hz);
 }
 
 // Push phase 2's values of a cluster tile to the CTAs that finish them (16-byte DSMEM
@@ -601,7 +763,7 @@ __device__ __forceinline__ void phase_3_out(int64_t out_base, const FusedArgs& a
 // `parity`: the input's first element is `in_elem0` (for the adjoint's diagonal) and the
 // outputs start at element `out_base`.  All threads of the CTA call this; it returns with
 // the CTA's output stores issued (a barrier is still needed before `buf` is refilled).
-template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE, bool TS = false>
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE, bool TS = false, bool HZ = false>
 __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base, const FusedArgs& args,
                                              uint32_t* buf, uint64_t* bar, uint32_t parity) {
   static_assert(CB == 0, "cluster tiles run in the pipelined cluster kernel");
@@ -621,6 +783,19 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
     if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
   }
 
+  // Haar side output (the HZ instantiations): row tiles of whole signals in dyadic order
+  static_assert(!HZ || (TLO == 0 && CB == 0 && OUTMODE == 0 && M >= 1), "side output of whole-signal row tiles");
+  constexpr int ZM = HZ ? M : 0;
+  constexpr bool ZEND = SCALE;
+  HaarZ hz{};
+  if constexpr (ZM > 0) {
+    if (args.haar_z != nullptr) {
+      hz.z = static_cast<uint32_t*>(args.haar_z) + out_base;
+      const int64_t left = args.out_total - out_base;
+      hz.limit = left < (int64_t{1} << TB) ? static_cast<uint32_t>(left) : (1u << TB);
+    }
+  }
+
   uint32_t v[64];
   auto scale_all = [&]() {
     if constexpr (SCALE) {
@@ -630,12 +805,12 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
   };
 
   if constexpr (F.has_p3) {
-    phases_1_2<TLO, M, TB, CB, BF, HM>(v, in_elem0, args, buf, bf);
+    phases_1_2<TLO, M, TB, CB, BF, HM, ZM, ZEND>(v, in_elem0, args, buf, bf, &hz);
     if constexpr (!F.b_is_s) __syncthreads();
     store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
     __syncthreads();
     load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, 0));
-    bfly<P3, 11, TLO + M, HM>(v, bf, lane, warp);
+    bfly<P3, 11, TLO + M, HM, BF, ZM, ZEND>(v, bf, lane, warp, &hz);
     scale_all();
     __syncthreads();
     store_phase<FW, P3, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
@@ -651,7 +826,7 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
         if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
       });
     }
-    bfly<P1, 0, (TLO + M < 5 ? TLO + M : 5), HM>(v, bf, lane, warp);
+    bfly<P1, 0, (TLO + M < 5 ? TLO + M : 5), HM, BF, ZM, ZEND>(v, bf, lane, warp, &hz);
     if constexpr (F.p1_final) {
       scale_all();
       __syncthreads();
@@ -661,7 +836,7 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
       store_phase<P1, P1, LS, LMASK>(v, buf, base);
       __syncthreads();
       load_phase<P2, LS, LMASK>(v, buf, thread_pos<P2, LS, LMASK>(lane, warp, 0));
-      bfly<P2, 5, TLO + M, HM>(v, bf, lane, warp);
+      bfly<P2, 5, TLO + M, HM, BF, ZM, ZEND>(v, bf, lane, warp, &hz);
       scale_all();
       __syncthreads();
       store_phase<FW, P2, LF, ~0u>(v, buf, thread_pos<FW, LF, ~0u>(lane, warp, 0));
@@ -682,7 +857,11 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
-        tma_store_4d(&args.tout, buf, 0, 0, 0, static_cast<int>(out_base >> (F.stage_s + 3)));
+        if (args.checked && !range_ok(out_base, int64_t{1} << TB, args.out_total)) {
+          check_fail(args.status, out_base);
+        } else {
+          tma_store_4d(&args.tout, buf, 0, 0, 0, static_cast<int>(out_base >> (F.stage_s + 3)));
+        }
         bulk_commit_group();
       }
       return;
@@ -716,7 +895,7 @@ constexpr int fused_ctas_per_sm() {
 // Persistent: each CTA walks the units u = first, first + stride, ... with two shared
 // buffers; the TMA load of unit k+1 is issued before unit k is transformed, so HBM reads
 // overlap the butterflies and the stores of the previous unit.
-template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE>
+template <int TLO, int M, int TB, int CB, class BF, bool SCALE, int OUTMODE, bool HZ = false>
 __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
     fused_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ FusedArgs args,
                  const int64_t units) {
@@ -735,8 +914,7 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
   const int64_t stride = gridDim.x;
   const int64_t first = blockIdx.x;
   auto elem0 = [&](int64_t u) { return unit_elem<TB>(args, args.in_off, u); };
-  auto row0 = [&](int64_t u) { return static_cast<int>(elem0(u) >> 5); };
-  if (threadIdx.x == 0 && first < units) tile_issue<TB>(&tin, row0(first), buf0, bar);
+  if (threadIdx.x == 0 && first < units) tile_issue_at<TB>(&tin, elem0(first), buf0, bar, args);
   int k = 0;
   for (int64_t u = first; u < units; u += stride, ++k) {
     uint32_t* cur = (k & 1) ? buf1 : buf0;
@@ -744,10 +922,10 @@ __global__ void __launch_bounds__(1 << (TB - 6), fused_ctas_per_sm<TB>())
     const int64_t un = u + stride;
     if (threadIdx.x == 0 && un < units) {
       if (args.tma_store) bulk_wait_read();  // the previous unit's TMA store has read `nxt`
-      tile_issue<TB>(&tin, row0(un), nxt, bar + ((k + 1) & 1));
+      tile_issue_at<TB>(&tin, elem0(un), nxt, bar + ((k + 1) & 1), args);
     }
-    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE, true>(elem0(u), unit_elem<TB>(args, args.out_off, u), args,
-                                                           cur, bar + (k & 1), (k >> 1) & 1);
+    tile_compute<TLO, M, TB, CB, BF, SCALE, OUTMODE, true, HZ>(elem0(u), unit_elem<TB>(args, args.out_off, u), args,
+                                                               cur, bar + (k & 1), (k >> 1) & 1);
     __syncthreads();
   }
   // no TMA load or store left in flight on shared memory, even after a wait gave up
@@ -810,7 +988,8 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
   // first input / output element of the unit of iteration k
   auto elem0 = [&](int64_t k) { return unit_elem<TB + CB>(args, args.in_off, first + k * stride); };
   auto oelem0 = [&](int64_t k) { return unit_elem<TB + CB>(args, args.out_off, first + k * stride); };
-  auto row0 = [&](int64_t k) { return static_cast<int>((elem0(k) + (int64_t{rank} << TB)) >> 5); };
+  auto cta_elem0 = [&](int64_t k) { return elem0(k) + (int64_t{rank} << TB); };
+  auto row0 = [&](int64_t k) { return static_cast<int>(cta_elem0(k) >> 5); };
   auto par = [](int64_t u) { return static_cast<uint32_t>((u / kClusterBufs) & 1); };
   BF bf{};
   if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
@@ -831,8 +1010,8 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
     }
   };
 
-  if (tid == 0 && K > 0) tile_issue<TB>(&tin, row0(0), buf(0), tma);
-  if (tid == 0 && K > 1) tile_issue<TB>(&tin, row0(1), buf(1), tma + 1);
+  if (tid == 0 && K > 0) tile_issue_at<TB>(&tin, cta_elem0(0), buf(0), tma, args);
+  if (tid == 0 && K > 1) tile_issue_at<TB>(&tin, cta_elem0(1), buf(1), tma + 1, args);
   if (tid < NR && K > 0) mbar_remote_arrive(freeb + 0, tid);  // buffer 2 (R_0) starts free
   for (int64_t k = 0; k <= K; ++k) {
     if (k >= 1) {
@@ -841,7 +1020,7 @@ __global__ void __launch_bounds__(1 << (TB - 6), 1)
       wait_cluster(fullb + u % kClusterBufs, par(u));
       phase_3_out<TLO, M, TB, CB, BF, SCALE, OUTMODE>(oelem0(u), args, buf(u + 2), rank, bf);
       __syncthreads();  // buffer (k+1) mod 3 is free: the copy-out has read it
-      if (tid == 0 && k + 1 < K) tile_issue<TB>(&tin, row0(k + 1), buf(k + 1), tma + (k + 1) % kClusterBufs);
+      if (tid == 0 && k + 1 < K) tile_issue_at<TB>(&tin, cta_elem0(k + 1), buf(k + 1), tma + (k + 1) % kClusterBufs, args);
     }
     if (k < K) {
       // ---- phases 1-2 of unit k, then push R_k

@@ -52,13 +52,13 @@ int64_t resident_units(K kern, int threads, int smem, int cluster) {
 
 int64_t persistent_cap_override();  // CHW_MAX_RESIDENT_UNITS, 0 = none (tuning)
 
-template <int TLO, int M, int TB, int CB, class BF, bool SC, int OM>
+template <int TLO, int M, int TB, int CB, class BF, bool SC, int OM, bool HZ = false>
 cudaError_t launch_fused(const CUtensorMap* tin, const FusedArgs& args, int64_t units, cudaStream_t st) {
   constexpr auto kern = [] {
     if constexpr (CB > 0)
       return cluster_kernel<TLO, M, TB, CB, BF, SC, OM>;
     else
-      return fused_kernel<TLO, M, TB, CB, BF, SC, OM>;
+      return fused_kernel<TLO, M, TB, CB, BF, SC, OM, HZ>;
   }();
   constexpr int smem = CB > 0 ? cluster_smem_bytes<TB>() : fused_smem_bytes<TB>();
   constexpr int threads = 1 << (TB - 6);
@@ -94,6 +94,10 @@ inline int stage_key(int tlo, int m, int tb, int cb, int om) { return make_plan(
 // table is generated by the build from its list of shapes, one translation unit per shape.
 FusedLaunchFn lookup_fused(int tlo, int m, int tb, int cb, int var, int om);
 
+// The single-CTA dyadic row kernel of m = 1..14 (tile bits tb) that also writes the Haar side
+// output z = Psi_m x to FusedArgs::haar_z (fused.cuh, HaarZ); nullptr for other shapes.
+FusedLaunchFn lookup_fused_hz(int m, int tb, int var);
+
 // The tensor-memory whole-signal kernel (tmem.cuh) for m = 15, 16 in dyadic (om = 0),
 // column-blocked two-pass rows (om = 1, FusedArgs::colblock_a), natural (om = 2) or
 // sequency (om = 3) order: `tin` maps the input as rows of 32 words
@@ -104,6 +108,16 @@ FusedLaunchFn lookup_fused(int tlo, int m, int tb, int cb, int var, int om);
 using TmemLaunchFn = cudaError_t (*)(const CUtensorMap* tin, const CUtensorMap* tout, const FusedArgs& args,
                                      int64_t units, cudaStream_t st);
 TmemLaunchFn lookup_tmem(int m, int var, int om);
+
+// The dyadic tensor-memory kernel (m = 15, 16) that also writes the Haar side output.
+TmemLaunchFn lookup_tmem_hz(int m, int var);
+
+// The same kernel on the column tiles of a two-pass split's second pass: units of 2^m words
+// (m = 15, 16) holding 2^clo columns x 2^(m-clo) rows of the first pass's column-blocked
+// output, transformed over the rows and written as 2^clo contiguous output rows in dyadic
+// order (tin, tout as for the dyadic whole-signal kernel).  clo = 5 for m = 15; 2..5 for
+// m = 16.  nullptr for other shapes.
+TmemLaunchFn lookup_tmem_col(int m, int clo, int var);
 
 }  // namespace chw
 

@@ -26,6 +26,7 @@ struct RaggedGroup {
 
 struct RaggedPlan {
   int64_t count = 0;
+  bool checked = false;
   std::vector<uint8_t> ms;
   std::vector<int64_t> off;  // count + 1 entries
   int64_t total = 0;
@@ -123,6 +124,8 @@ cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, int64_t coun
     if (!fn) return cudaErrorInvalidValue;
     FusedArgs a{};
     a.status = r->d_status;
+    a.checked = r->checked;
+    a.in_total = r->total;
     a.out = y;
     a.out_total = r->total;
     a.end_scale = end_scale_host(m);
@@ -145,6 +148,8 @@ cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, int64_t coun
     const int64_t cnt = std::min(chunk, count - s0);
     FusedArgs p1{};
     p1.status = r->d_status;
+    p1.checked = r->checked;
+    p1.in_total = r->total;
     p1.out = r->d_scratch;
     p1.out_total = cnt << m;
     p1.end_scale = 1.0f;
@@ -155,6 +160,8 @@ cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, int64_t coun
     if (e != cudaSuccess) return e;
     FusedArgs p2{};
     p2.status = r->d_status;
+    p2.checked = r->checked;
+    p2.in_total = cnt << m;
     p2.out = y;
     p2.out_total = r->total;
     p2.end_scale = end_scale_host(m);
@@ -219,8 +226,7 @@ void tune_groups(RaggedPlan* r) {
 
 }  // namespace
 
-RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, bool tune, std::string* why) {
-  std::vector<int64_t> off(count + 1);
+void ragged_pack(const uint8_t* ms, int64_t count, int64_t* off) {
   int64_t o = 0;
   for (int64_t i = 0; i < count; ++i) {
     off[i] = o;
@@ -228,13 +234,19 @@ RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_
     o = (o + 31) & ~int64_t{31};  // every signal starts on a 128-byte boundary
   }
   off[count] = o;
-  return ragged_create_at(ms, off.data(), count, o, variant, d_status, tune, why);
+}
+
+RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, bool tune, std::string* why) {
+  std::vector<int64_t> off(count + 1);
+  ragged_pack(ms, count, off.data());
+  return ragged_create_at(ms, off.data(), count, off[count], variant, d_status, tune, why);
 }
 
 RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t count, int64_t total, int variant,
-                             int* d_status, bool tune, std::string* why) {
+                             int* d_status, bool tune, std::string* why, bool checked) {
   auto* r = new RaggedPlan();
   r->count = count;
+  r->checked = checked;
   r->ms.assign(ms, ms + count);
   r->off.assign(offsets, offsets + count);
   r->off.push_back(total);
@@ -342,6 +354,9 @@ int ragged_run(RaggedPlan* r, const void* x, void* y, cudaStream_t st, std::stri
     a.off = r->d_off;
     a.x = static_cast<const uint32_t*>(x);
     a.y = static_cast<uint32_t*>(y);
+    a.total = r->total;
+    a.checked = r->checked;
+    a.status = r->d_status;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal);
     cudaError_t le = cudaSuccess;

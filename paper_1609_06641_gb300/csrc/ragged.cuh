@@ -41,16 +41,23 @@ struct RaggedArgs {
   const int64_t* off;
   const uint32_t* x;
   uint32_t* y;
+  int64_t total;  // elements of x and y (checked mode: each signal must lie inside)
+  int checked;    // CHW_FLAG_CHECKED
+  int* status;
 };
 
 struct RaggedPlan;
 // `tune`: time each length group's configurations (tile size, cluster or two passes, the
 // two-pass split) on temporary arrays of the plan's size and keep the fastest.
 RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, bool tune, std::string* why);
+// The library's packing of `count` signals: offsets[i] (count + 1 entries, the last one the
+// total), each signal starting on a 32-element (128-byte) boundary.
+void ragged_pack(const uint8_t* ms, int64_t count, int64_t* offsets);
 // The same over caller-chosen offsets (elements of x and y; `total` = their length): signals
-// with m >= 13 must start on a 32-element boundary, shorter ones anywhere.
+// with m >= 13 must start on a 32-element boundary, shorter ones anywhere.  `checked`: the
+// kernels range-check every offset they use (CHW_FLAG_CHECKED).
 RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t count, int64_t total, int variant,
-                             int* d_status, bool tune, std::string* why);
+                             int* d_status, bool tune, std::string* why, bool checked = false);
 void ragged_destroy(RaggedPlan* r);
 int64_t ragged_total(const RaggedPlan* r);
 int ragged_passes(const RaggedPlan* r);

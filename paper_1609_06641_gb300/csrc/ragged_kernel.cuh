@@ -15,6 +15,10 @@ __device__ void small_group(const RaggedArgs& a, const RaggedTask& task, uint32_
     const int m = a.ms[s];
     const int n = 1 << m;
     const int64_t off = a.off[s];
+    if (a.checked && !(off >= 0 && off <= a.total - n)) {  // the same decision in every thread
+      if (threadIdx.x == 0) check_fail(a.status, off);
+      continue;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) buf[i] = a.x[off + i];
     for (int t = 0; t < m; ++t) {

@@ -13,11 +13,20 @@
 // register labels it holds the R values that differ only in the row bits, and runs the
 // cascade's last butterflies (bits 14..M-1) in registers, with no exchange between
 // threads or SMs.  Results are staged in shared memory, one 2^14-value chunk at a time:
-// in dyadic or natural order they leave by TMA tensor stores that drain while the SM
-// transforms the next row; in sequency order the SM copies each aligned 32-element block
-// to its gray^{-1} block.  Each output chunk of a signal is interleaved with a row of the
+// in dyadic, natural or sequency order they leave by TMA tensor stores that drain while
+// the SM transforms the next row (sequency order stages each chunk already permuted by
+// gray^{-1}, see the output chunk below).  Each output chunk of a signal is interleaved with a row of the
 // next signal (alternating tensor-memory column layouts), so every step loads one row and
 // stores one chunk.
+//
+// The same kernel runs the column pass of the two-pass split y = H_b X^T H_a (CLO > 0): a
+// unit is then a column block of 2^a rows x 2^CLO columns (M = a + CLO words, contiguous
+// in the first pass's column-blocked output), label bits 0..CLO-1 the column and bits
+// CLO..M-1 the row.  Only the row bits are transformed (the first phase starts at label
+// bit CLO, or is skipped when CLO = 5), and column c's results form the contiguous output
+// row c in dyadic order: label (c, r) is stored at c 2^a + bitrev_a(r).  Label bits 8..M-1
+// then land on output bits M-1-b exactly as in the whole-signal case; only the run index
+// of a thread (its output bits M-8..M-1) is formed differently.
 //
 // Tensor memory is 128 lanes x 512 columns x 4 bytes = 256 KB per SM: one 2^16-word
 // signal.  Shared memory holds two 64 KB row buffers (the next rows' TMA loads overlap
@@ -38,6 +47,18 @@ constexpr uint32_t bitrev_bits(uint32_t x, int n) {
   for (int i = 0; i < n; ++i) r |= ((x >> i) & 1u) << (n - 1 - i);
   return r;
 }
+
+// gray^{-1}(x): bit i is the XOR of the bits i, i+1, ... of x (sequency order).
+constexpr uint32_t gray_inverse(uint32_t x) {
+  x ^= x >> 1;
+  x ^= x >> 2;
+  x ^= x >> 4;
+  x ^= x >> 8;
+  x ^= x >> 16;
+  return x;
+}
+
+constexpr uint32_t parity_of(uint32_t x) { return gray_inverse(x) & 1u; }
 
 // Phase 3 of the row (label bits 11..13) with the registers on label bits 8..13 and the
 // threads on bits 0..7; lane bits 0..2 carry label bits 7, 6, 5, which are the low bits of
@@ -153,6 +174,29 @@ struct TmemCfg {
   static_assert(OM == 0 || natural_ok(), "a natural-order chunk is 64 rows of one 256-word block");
 };
 
+// Phases 1 and 2 of a 2^14-word row with the butterflies of label bits LO..10 (LO <= 5):
+// the fused row tile's phases, the first one restricted to bits LO..4 (skipped when LO = 5,
+// phase 2 then reading the TMA layout directly).  On return v holds phase 2's values.
+template <int LO, class BF>
+__device__ __forceinline__ void row_phases_from(uint32_t (&v)[64], uint32_t* buf, const BF& bf) {
+  using Cfg = FusedCfg<0, kTmemTB, kTmemTB, 0>;
+  constexpr FusedPlan F = Cfg::plan;
+  constexpr uint32_t LMASK = Cfg::LMASK;
+  constexpr Phase P1 = F.p1, P2 = F.p2;
+  constexpr Lin LS = F.lin_s;
+  static_assert(LO >= 1 && LO <= 5, "column tiles start at label bit 1..5");
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if constexpr (LO < 5) {
+    const uint32_t base = thread_pos<P1, LS, LMASK>(lane, warp, 0);
+    load_phase<P1, LS, LMASK>(v, buf, base);
+    butterflies<P1, LO, 5>(v, bf);
+    store_phase<P1, P1, LS, LMASK>(v, buf, base);
+    __syncthreads();
+  }
+  load_phase<P2, LS, LMASK>(v, buf, thread_pos<P2, LS, LMASK>(lane, warp, 0));
+  butterflies<P2, 5, 11>(v, bf);
+}
+
 constexpr int tmem_smem_bytes() {
   return (12 << kTmemTB) + 1024 + 64;  // two row buffers and the staging buffer, barriers, slot
 }
@@ -178,12 +222,18 @@ __device__ __forceinline__ uint32_t tmem_col(uint32_t par, int r, int k) {
   }
 }
 
-template <int M, class BF, bool SCALE, int OM>
+template <int M, class BF, bool SCALE, int OM, int CLO = 0, bool HZ = false>
 __global__ void __launch_bounds__(kTmemThreads, 1)
     tmem_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                 const FusedArgs args, const int64_t units) {
+  static_assert(CLO == 0 || (OM == 0 && CLO >= 2 && CLO <= 5 && M - CLO >= 10),
+                "column tiles: dyadic rows of 2^(M-CLO) >= 2^10 outputs, 4..32 columns");
   using T = TmemCfg<M, OM>;
   constexpr int TB = T::TB, R = T::R, JW = T::JW;
+  // Haar side output (FusedArgs::haar_z; the HZ instantiations, whole signals, dyadic order)
+  static_assert(!HZ || (CLO == 0 && OM == 0), "side output of whole signals in dyadic order");
+  constexpr int ZM = HZ ? M : 0;
+  static_assert(ZM == 0 || reg_label(T::P3, 0) == 0u, "chunk 0, register 0 holds labels with bits 8..13 zero");
   constexpr uint32_t LMASK = (1u << TB) - 1u;
   constexpr Phase P2 = T::P2, P3 = T::P3;
   constexpr Lin LB = T::LB;
@@ -215,10 +265,10 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   const int64_t K = first < units ? (units - first + stride - 1) / stride : 0;
   const int64_t G = K * R;  // rows this CTA loads
   auto elem0 = [&](int64_t k) { return unit_elem<M>(args, args.in_off, first + k * stride); };
-  auto row0 = [&](int64_t g) { return static_cast<int>((elem0(g / R) >> 5) + (g % R) * (1 << (TB - 5))); };
+  auto rowe = [&](int64_t g) { return elem0(g / R) + ((g % R) << TB); };  // first element of row g
   if (tid == 0) {
-    if (G > 0) tile_issue<TB>(&tin, row0(0), bufs, bar);
-    if (G > 1) tile_issue<TB>(&tin, row0(1), bufs + (1u << TB), bar + 1);
+    if (G > 0) tile_issue_at<TB>(&tin, rowe(0), bufs, bar, args);
+    if (G > 1) tile_issue_at<TB>(&tin, rowe(1), bufs + (1u << TB), bar + 1, args);
   }
   BF bf{};
   if constexpr (std::is_same_v<BF, BfF32PerLevel>) bf.c = 0.70710678118654752440f;
@@ -228,7 +278,10 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   // dyadic: output run of this thread (output bits M-8..M-1) and its staging swizzle;
   // natural: its label bits 0..7 are its output bits 0..7
   const uint32_t tl = thread_label<P3>(lane, warp, 0);
-  const uint32_t rho = bitrev_bits(tl, 8);
+  // column tiles: output bits M-8..M-1 are the column (label bits 0..CLO-1) above
+  // bitrev of the row's label bits CLO..7
+  const uint32_t rho = CLO == 0 ? bitrev_bits(tl, 8)
+                                : ((tl & ((1u << CLO) - 1u)) << (8 - CLO)) | bitrev_bits(tl >> CLO, 8 - CLO);
   const uint32_t sxor = (rho & 7u) << 2;
 
   // Row r of signal k: label bits 0..13, then into tensor memory.
@@ -240,14 +293,27 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
     }
     uint32_t v[64];
-    phases_1_2<0, TB, TB, 0, BF>(v, elem0(k) + (int64_t{r} << TB), args, buf, bf);
+    // Haar side output of a whole signal: this row's labels carry the row number above bit 13
+    HaarZ hz{};
+    if constexpr (ZM > 0) {
+      if (args.haar_z != nullptr) {
+        hz.z = static_cast<uint32_t*>(args.haar_z) + unit_elem<M>(args, args.out_off, first + k * stride);
+        hz.hi = static_cast<uint32_t>(r) << TB;
+        hz.limit = 1u << M;
+      }
+    }
+    if constexpr (CLO == 0) {
+      phases_1_2<0, TB, TB, 0, BF, 0, ZM, SCALE>(v, elem0(k) + (int64_t{r} << TB), args, buf, bf, &hz);
+    } else {
+      row_phases_from<CLO>(v, buf, bf);
+    }
     if constexpr (!T::b_is_s) __syncthreads();
     store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
     __syncthreads();
     load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, 0));
-    butterflies<P3, 11, TB>(v, bf);
+    bfly<P3, 11, TB, 0, BF, ZM, SCALE>(v, bf, lane, warp, &hz);
     __syncthreads();  // the row buffer is no longer read: refill it
-    if (tid == 0 && g + 2 < G) tile_issue<TB>(&tin, row0(g + 2), buf, bar + (g & 1));
+    if (tid == 0 && g + 2 < G) tile_issue_at<TB>(&tin, rowe(g + 2), buf, bar + (g & 1), args);
     const uint32_t par = static_cast<uint32_t>(k & 1);
     tmem_st16<0>(taddr + tmem_col<M>(par, r, 0), v);
     tmem_st16<16>(taddr + tmem_col<M>(par, r, 16), v);
@@ -273,6 +339,13 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     tmem_wait_ld<16>(u);
     tmem_wait_ld<32>(u);
     tmem_wait_ld<48>(u);
+    // Haar side output of the last label bits: the labels whose bits 0..13 are zero are
+    // register 0 of output chunk 0 of the thread with label 0, one per row
+    uint32_t* zs = nullptr;
+    if constexpr (ZM > 0 && q == 0) {
+      if (args.haar_z != nullptr && tl == 0u)
+        zs = static_cast<uint32_t*>(args.haar_z) + unit_elem<M>(args, args.out_off, first + k * stride);
+    }
     sfor<M - TB>([&](auto bb) {  // label bit TB + b pairs rows r and r + 2^b
       constexpr int b = bb;
       sfor<R>([&](auto rr) {
@@ -281,7 +354,27 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
           sfor<JW>([&](auto j) { bf(u[r * JW + j], u[(r | (1 << b)) * JW + j]); });
         }
       });
+      if constexpr (ZM > 0 && q == 0) {
+        if (zs != nullptr) {  // rows with bit b set and bits below it zero: level TB + b + 1
+          sfor<R>([&](auto rr) {
+            constexpr int r = rr;
+            if constexpr ((r & ((2 << b) - 1)) == (1 << b)) {
+              constexpr float sc = end_scale_const(TB + b + 1);
+              uint32_t val = u[r * JW];
+              if constexpr (SCALE) val = __float_as_uint(__fmul_rn(__uint_as_float(val), sc));
+              zs[(1u << (M - TB - b - 1)) + (static_cast<uint32_t>(r) >> (b + 1))] = val;
+            }
+          });
+        }
+      }
     });
+    if constexpr (ZM > 0 && q == 0) {
+      if (zs != nullptr) {  // the approximation: label 0 after every level
+        uint32_t val = u[0];
+        if constexpr (SCALE) val = __float_as_uint(__fmul_rn(__uint_as_float(val), end_scale_const(M)));
+        zs[0] = val;
+      }
+    }
     if constexpr (SCALE) {
 #pragma unroll
       for (int i = 0; i < 64; ++i) u[i] = __float_as_uint(__fmul_rn(__uint_as_float(u[i]), args.end_scale));
@@ -310,14 +403,71 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
-        const int y = static_cast<int>(ob >> (M - 6));
+        if (args.checked && !range_ok(ob, int64_t{1} << M, args.out_total)) {
+          check_fail(args.status, ob);
+        } else {
+          const int y = static_cast<int>(ob >> (M - 6));
 #pragma unroll
-        for (int b = 0; b < 8; ++b) tma_store_2d(&tout, stage + (b << 11), static_cast<int>(qo) * 256 + 32 * b, y);
+          for (int b = 0; b < 8; ++b) tma_store_2d(&tout, stage + (b << 11), static_cast<int>(qo) * 256 + 32 * b, y);
+        }
+        bulk_commit_group();
+      }
+    } else if constexpr (OM == 3) {
+      // Sequency order: dyadic position p = rho 2^L + 64 q + w (L = M - 8) is stored at
+      // gray^{-1}(p).  Its run is dr = gray^{-1}(rho); inside the run the 64-word segment is
+      // gray^{-1}(q), complemented when dr is odd; inside the segment the 4-word group c of w
+      // goes to gray^{-1}(c), complemented when parity(q) differs from dr's parity, and its
+      // four words are reordered by parity(c) against that.  So the chunk is staged in its
+      // final order as four TMA boxes (even or odd destination runs, 128 rows each, times the
+      // two 32-word halves of the segment) and leaves through the 3-D view {2^L words, run
+      // parity, run pair} of the output, like the other orders, off the SM's store path.
+      constexpr uint32_t L = M - 8;
+      constexpr uint32_t qmask = (1u << (L - 6)) - 1u;
+      constexpr uint32_t gq = gray_inverse(q), pq = parity_of(q);
+      const uint32_t dr = gray_inverse(rho);
+      const uint32_t pd = dr & 1u, zr = dr >> 1, zx = zr & 7u;
+      const uint32_t fx = pq ^ pd;                 // complement inside the segment
+      const uint32_t qd = gq ^ (pd ? qmask : 0u);  // the segment in the destination run
+      if (tid == 0) bulk_wait_read();  // the previous chunk's TMA stores have read the buffer
+      __syncthreads();
+      uint32_t* srow = stage + (pd << (TB - 2)) + (zr << 5);
+      sfor<16>([&](auto cc) {
+        constexpr int c = cc;
+        constexpr int s0 = T::src(q, 4 * c), s1 = T::src(q, 4 * c + 1);
+        constexpr int s2 = T::src(q, 4 * c + 2), s3 = T::src(q, 4 * c + 3);
+        constexpr uint32_t gc = gray_inverse(c), pc = parity_of(c);
+        const uint32_t C = gc ^ (fx ? 15u : 0u);
+        uint4 val = (pc ^ fx) ? make_uint4(u[s2], u[s3], u[s1], u[s0]) : make_uint4(u[s0], u[s1], u[s3], u[s2]);
+        if (args.diag_out != nullptr) {  // D acts on the stored positions
+          const int64_t at = ob + ((static_cast<int64_t>(dr) << L) | (qd << 6) | (C << 2));
+          const int8_t* dg = args.diag_out + (at & args.diag_mask);
+          uint32_t* e[4] = {&val.x, &val.y, &val.z, &val.w};
+#pragma unroll
+          for (int f = 0; f < 4; ++f)
+            if (dg[f] < 0) *e[f] = std::is_same_v<BF, BfI32> ? 0u - *e[f] : *e[f] ^ 0x80000000u;
+        }
+        *reinterpret_cast<uint4*>(srow + ((C >> 3) << (TB - 1)) + (((C & 7u) ^ zx) << 2)) = val;
+      });
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0 && args.checked && !range_ok(ob, int64_t{1} << M, args.out_total)) {
+        check_fail(args.status, ob);
+        bulk_commit_group();
+      } else if (tid == 0) {
+        const int z = static_cast<int>(ob >> (L + 1));
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            tma_store_3d(&tout, stage + (h << (TB - 1)) + (pp << (TB - 2)),
+                         static_cast<int>(64 * (gq ^ (pp ? qmask : 0u)) + 32 * h), pp, z);
         bulk_commit_group();
       }
     } else {
       if (OM == 0 && args.diag_out != nullptr) {  // D acts on the stored positions
-        const int8_t* d = args.diag_out + ((static_cast<int64_t>(rho) << (M - 8)) & args.diag_mask);
+        // (a column tile's outputs are a part of a longer signal: its place in it counts)
+        const int64_t at = (CLO > 0 ? ob : 0) + (static_cast<int64_t>(rho) << (M - 8));
+        const int8_t* d = args.diag_out + (at & args.diag_mask);
         sfor<64>([&](auto ww) {
           constexpr int w = ww;
           constexpr int si = T::src(q, w);
@@ -340,58 +490,62 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
-          const int y = static_cast<int>(ob >> (M - 8));
-          tma_store_2d(&tout, stage, 64 * q, y);
-          tma_store_2d(&tout, stage + (1u << (TB - 1)), 64 * q + 32, y);
+          if (args.checked && !range_ok(ob, int64_t{1} << M, args.out_total)) {
+            check_fail(args.status, ob);
+          } else {
+            const int y = static_cast<int>(ob >> (M - 8));
+            tma_store_2d(&tout, stage, 64 * q, y);
+            tma_store_2d(&tout, stage + (1u << (TB - 1)), 64 * q + 32, y);
+          }
+          bulk_commit_group();
+        }
+      } else if (OM == 1 && args.tma_store) {
+        // Column blocks of 32: the 32-word segment g of row r (signal s) lives at
+        // s 2^(a+M) + g 2^(a+5) + 32 r.  The staged boxes hold, for every run rho, the
+        // segments g = rho 2^(M-13) + 2q + h (box h), so each box is one tensor store through
+        // the 5-D view {32 words, r, g mod 2^(M-13), rho, s} of the scratch.
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          const int64_t u = first + k * stride;
+          const int cba = args.colblock_a;
+          const int64_t sig0 = (u >> cba) << (cba + M);
+          if (args.checked && !range_ok(sig0, int64_t{1} << (cba + M), args.out_total)) {
+            check_fail(args.status, sig0);
+          } else {
+            const int r = static_cast<int>(u & ((int64_t{1} << cba) - 1)), s = static_cast<int>(u >> cba);
+            tma_store_5d(&tout, stage, 0, r, 2 * q, 0, s);
+            tma_store_5d(&tout, stage + (1u << (TB - 1)), 0, r, 2 * q + 1, 0, s);
+          }
           bulk_commit_group();
         }
       } else {
-        // Sequency order scatters the runs (gray^{-1} of their high bits), and the
-        // column-blocked order of the first of two passes sends every 32-element segment of
-        // a row to its own block, so the chunk goes out through the SM: a warp copies four
-        // aligned 32-element blocks, each to one whole 128-byte line (gray^{-1} maps an
-        // aligned block onto an aligned block, reordered inside).
+        // The column-blocked order of the first of two passes sends every 2^w-element
+        // segment of a row to its own block, so the chunk goes out through the SM: a warp
+        // copies four aligned 32-element pieces of the staged chunk.
+        static_assert(OM == 1, "dyadic, natural and sequency chunks leave by TMA stores");
         __syncthreads();
         uint32_t* out = static_cast<uint32_t*>(args.out);
         // OM = 1: row u is row r = u mod 2^a of signal u / 2^a (a = colblock_a); its element
-        // k goes to signal * 2^(a+M) + (k / 32) 2^(a+5) + 32 r + k mod 32
+        // k goes to signal * 2^(a+M) + (k / 2^w) 2^(a+w) + 2^w r + k mod 2^w, 2^w = the
+        // column block's width (w = colblock_c, 32 columns by default)
         const int64_t u = first + k * stride;
         const int cba = args.colblock_a;
-        const int64_t cb_base = ((u >> cba) << (cba + M)) + ((u & ((int64_t{1} << cba) - 1)) << 5);
+        const int cbw = args.colblock_c != 0 ? args.colblock_c : 5;
+        const int64_t cb_base = ((u >> cba) << (cba + M)) + ((u & ((int64_t{1} << cba) - 1)) << cbw);
+        // every address below lies in the signal's 2^(a+M) elements: checked once
+        const int64_t sig0 = (u >> cba) << (cba + M);
+        const bool skip = args.checked && !range_ok(sig0, int64_t{1} << (cba + M), args.out_total);
+        if (skip && tid == 0) check_fail(args.status, sig0);
 #pragma unroll 4
-        for (int i = static_cast<int>(tid); i < (1 << (TB - 2)); i += kTmemThreads) {
+        for (int i = skip ? (1 << (TB - 2)) : static_cast<int>(tid); i < (1 << (TB - 2)); i += kTmemThreads) {
           const uint32_t h = static_cast<uint32_t>(i) >> (TB - 3), run = (static_cast<uint32_t>(i) >> 3) & 255u;
           const uint32_t c8 = static_cast<uint32_t>(i) & 7u;
           uint4 val = *reinterpret_cast<const uint4*>(stage + (h << (TB - 1)) + (run << 5) + ((c8 ^ (run & 7u)) << 2));
           // dyadic position / 4 within the signal
           const uint32_t p4 = (run << (M - 10)) | static_cast<uint32_t>(16 * q) | (h << 3) | c8;
-          int64_t addr;
-          if constexpr (OM == 1) {
-            addr = cb_base + (static_cast<int64_t>(p4 >> 3) << (cba + 5)) + ((p4 & 7u) << 2);
-          } else {
-            uint32_t g = p4;  // gray^{-1}
-            g ^= g >> 1;
-            g ^= g >> 2;
-            g ^= g >> 4;
-            g ^= g >> 8;
-            g ^= g >> 16;
-            val = (__popc(p4) & 1) ? make_uint4(val.z, val.w, val.y, val.x) : make_uint4(val.x, val.y, val.w, val.z);
-            addr = ob + (static_cast<int64_t>(g) << 2);
-          }
-          if (args.diag_out != nullptr) {  // D acts on the stored positions
-            const int8_t* d = args.diag_out + (addr & args.diag_mask);
-            if constexpr (std::is_same_v<BF, BfI32>) {
-              if (d[0] < 0) val.x = 0u - val.x;
-              if (d[1] < 0) val.y = 0u - val.y;
-              if (d[2] < 0) val.z = 0u - val.z;
-              if (d[3] < 0) val.w = 0u - val.w;
-            } else {
-              if (d[0] < 0) val.x ^= 0x80000000u;
-              if (d[1] < 0) val.y ^= 0x80000000u;
-              if (d[2] < 0) val.z ^= 0x80000000u;
-              if (d[3] < 0) val.w ^= 0x80000000u;
-            }
-          }
+          const uint32_t e = p4 << 2;  // a 4-word chunk never straddles a block (w >= 2)
+          const int64_t addr = cb_base + (static_cast<int64_t>(e >> cbw) << (cba + cbw)) + (e & ((1u << cbw) - 1u));
           st_global_v4(out + addr, val.x, val.y, val.z, val.w);
         }
       }

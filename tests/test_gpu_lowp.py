@@ -78,8 +78,37 @@ def test_lowp_fused_tier_and_adjoint(chw, fmt, m):
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
-def test_lowp_per_level(chw, fmt):
-    check(chw, 11, 16, fmt, "per_level", seed=3)
+@pytest.mark.parametrize("m", [11, 12])
+def test_lowp_per_level(chw, fmt, m):
+    check(chw, m, 16, fmt, "per_level", seed=3 + m)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+@pytest.mark.parametrize("m", [11, 12])
+def test_lowp_adjoint_with_input_diagonal(chw, fmt, m):
+    # H^T D y: D flips the signs of the input codes, then the same transform and rounding
+    x64 = W.heavy_tailed_f64(m, 12, 70 + m)
+    bits, e_in = W.quantise_pow2(x64, fmt)
+    d = W.diag_pm1(m, 8)
+    qb, e_out = run_lowp(chw, bits, e_in, m, fmt, adjoint=True, diag=d)
+    flipped = bits ^ np.where(d < 0, np.uint16(0x8000), np.uint16(0))[None, :]
+    rb, re = O.lowp_forward_reference(flipped, e_in, m, fmt)
+    assert np.array_equal(e_out, re) and np.array_equal(qb, rb)
+
+
+@pytest.mark.parametrize("m", [11, 12])
+def test_lowp_bf16_subnormal_codes(chw, m):
+    # bf16 codes of magnitude below 2^-126 (subnormal): max|u| < 2^-120, so the output
+    # scaling 2^(K - E) lies outside fp32's normal range and takes two multiplies; the
+    # arithmetic keeps subnormals (no flush to zero), as the oracle's fp32 does
+    rng = np.random.default_rng(11 + m)
+    mag = rng.integers(1, 0x80, size=(6, 1 << m), dtype=np.uint16)  # bf16 subnormal patterns
+    bits = mag | np.where(rng.random((6, 1 << m)) < 0.5, np.uint16(0x8000), np.uint16(0))
+    bits[1, :] = 0x0001  # one all-equal signal: its transform is a single nonzero entry
+    e_in = rng.integers(-5, 5, 6).astype(np.int32)
+    qb, e_out = run_lowp(chw, bits, e_in, m, "bf16")
+    rb, re = O.lowp_forward_reference(bits, e_in, m, "bf16")
+    assert np.array_equal(e_out, re) and np.array_equal(qb, rb)
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])

@@ -115,7 +115,7 @@ def test_ordered_forced_two_pass(chw, order, m):
 
 
 @pytest.mark.parametrize("order", ["natural", "sequency"])
-@pytest.mark.parametrize("m,batch", [(4, 3), (10, 16), (14, 4), (16, 3), (19, 2)])
+@pytest.mark.parametrize("m,batch", [(4, 3), (10, 16), (14, 4), (15, 5), (16, 3), (19, 2)])
 def test_ordered_diag_adjoint_inplace(chw, order, m, batch):
     x = _x(m, batch, "f32", 6300 + m)
     d = W.diag_pm1(m, 6400 + m)

@@ -47,20 +47,30 @@ def test_one_pass_candidates(chw, m):
     assert chw.chw_tune_candidates(m, "f32", "end", order="natural") == []  # one kernel only
 
 
-@pytest.mark.parametrize("m", [17, 18, 20, 23, 24, 28])
+@pytest.mark.parametrize("m", [17, 18, 20, 23, 24, 28, 29, 30])
 @pytest.mark.parametrize("order", ["dyadic", "natural", "sequency"])
 def test_two_pass_candidates_are_valid_splits(chw, m, order):
     c = chw.chw_tune_candidates(m, "f32", "per_level", order=order)
     if order == "natural" and m >= 23:
         assert c == []  # m = 23: a = 9, b = 14 is the only natural split compiled; beyond: none
         return
+    if m == 30 or (m == 29 and order == "sequency"):
+        # one configuration, nothing to choose: dyadic m = 30 has only the split a = 14,
+        # b = 16; sequency order's column kernels take a <= 12 and its row kernels b <= 17
+        # (m = 29: a = 12 only; m = 30: none)
+        assert c == []
+        return
     two = [x for x in c if x[0] == TIER_TWO_PASS]
     assert two, (m, order)
     for _, b, tb in two:
         a = m - b
-        assert 6 <= a <= 12 and 5 <= b <= 17 and tb in (13, 14)
+        assert 6 <= a <= 14 and 5 <= b <= 17 and tb in (13, 14)
+        if a > 12:  # only tensor-memory column tiles (narrow blocks) take a = 13, 14, after
+            assert order == "dyadic" and b in (15, 16) and tb == 14  # a tensor-memory first pass
         if order == "natural":
             assert b <= 14 and a <= 9  # the natural-order kernels that exist
+    if order == "dyadic" and m >= 26:
+        assert (TIER_TWO_PASS, 16, 14) in c  # the built-in split a = m - 16
     assert len(set(c)) == len(c)
     if m == 17 and order != "natural":
         assert (TIER_CLUSTER, 17, 14) in c
