@@ -46,8 +46,8 @@ def _forward(chw, p, x):
 
 CASES = [
     (14, 40, "f32", "end", "dyadic"),
-    (16, 24, "f32", "end", "dyadic"),
-    (15, 9, "i32", "none", "sequency"),
+    (18, 5, "f32", "end", "dyadic"),
+    (20, 3, "i32", "none", "sequency"),
     (17, 6, "f32", "per_level", "dyadic"),
     (17, 4, "f32", "end", "natural"),
     (19, 3, "i32", "none", "dyadic"),
@@ -95,6 +95,10 @@ def test_every_candidate_is_bit_exact(chw):
 def test_single_configuration_is_not_timed(chw):
     p = chw.chw_plan(12, 8, "f32", "end", chw.CHW_FLAG_AUTOTUNE)
     assert chw.chw_plan_get_info(p).tuned == 0
+    # m = 16: the tensor-memory kernel is the only candidate
+    p16 = chw.chw_plan(16, 8, "f32", "end", chw.CHW_FLAG_AUTOTUNE)
+    i16 = chw.chw_plan_get_info(p16)
+    assert i16.tuned == 0 and i16.tier == 7
 
 
 def test_tuned_ragged_plan_is_bit_exact(chw):
