@@ -643,10 +643,13 @@ def main():
     e2e_steps = max(1, min(args.steps, 10))
     chw.chw_forward_host(plan, xh, yh)
     barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        chw.chw_forward_host(plan, xh, yh)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    reps = []
+    for _ in range(3):  # the median of three runs of e2e_steps calls (the host link varies)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            chw.chw_forward_host(plan, xh, yh)
+        reps.append((time.perf_counter() - t0) / e2e_steps)
+    e2e_s = sorted(reps)[1]
     e2e_s = max_over_ranks(e2e_s, world, dev)
     if not torch.equal(yh, y.cpu()):
         raise RuntimeError("host-buffer path disagrees with the device path")
@@ -656,15 +659,18 @@ def main():
     bufs = [torch.empty(rows, x.shape[1], device=dev) for _ in range(3)]
     streams = [torch.cuda.Stream() for _ in range(3)]
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        for i, r0 in enumerate(range(0, x.shape[0], rows)):
-            n_r = min(rows, x.shape[0] - r0)
-            with torch.cuda.stream(streams[i % 3]):
-                bufs[i % 3][:n_r].copy_(xh[r0: r0 + n_r], non_blocking=True)
-                yh[r0: r0 + n_r].copy_(bufs[i % 3][:n_r], non_blocking=True)
-        torch.cuda.synchronize()
-    link_s = (time.perf_counter() - t0) / e2e_steps
+    reps = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for i, r0 in enumerate(range(0, x.shape[0], rows)):
+                n_r = min(rows, x.shape[0] - r0)
+                with torch.cuda.stream(streams[i % 3]):
+                    bufs[i % 3][:n_r].copy_(xh[r0: r0 + n_r], non_blocking=True)
+                    yh[r0: r0 + n_r].copy_(bufs[i % 3][:n_r], non_blocking=True)
+            torch.cuda.synchronize()
+        reps.append((time.perf_counter() - t0) / e2e_steps)
+    link_s = sorted(reps)[1]
     del bufs
 
     if rank != 0:

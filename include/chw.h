@@ -82,9 +82,9 @@ typedef enum chw_norm_e {
                                     /* withholds a signal and waits give up after a few    */
                                     /* thousand polls, so chw_last_device_status() reports */
                                     /* CHW_ERR_TIMEOUT; the output is then undefined       */
-#define CHW_FLAG_CLUSTER 128u       /* m = 15..17: thread-block-cluster (DSMEM) tier instead */
-                                    /* of the tensor-memory tier (15, 16) or the two-pass  */
-                                    /* split (17)                                          */
+#define CHW_FLAG_CLUSTER 128u       /* m = 15..17: thread-block-cluster (DSMEM) tier of     */
+                                    /* shared-memory tiles instead of the tensor-memory    */
+                                    /* tier (one SM per signal at 15, 16; two at 17)       */
 #define CHW_FLAG_AUTOTUNE 256u      /* pick the tier, two-pass split and CTA tile by timing */
                                     /* the candidates (chw_tune_candidates) on the device  */
                                     /* when the plan is made; CHW_AUTOTUNE=1 in the        */
@@ -116,7 +116,9 @@ typedef struct chw_plan_info_s {
   int norm;                  /* chw_norm_t                                             */
   int tier;                  /* 0 simple, 1 fused CTA, 2 fused cluster, 3 two-pass, 4 ragged,
                                 5 fused 16-bit, 6 row-stack (one CTA, L2-resident rows),
-                                7 tensor memory (one CTA per signal, m = 15, 16)        */
+                                7 tensor memory (one CTA per signal, m = 15, 16),
+                                8 tensor memory over a cluster (m = 17: two SMs hold a
+                                  signal and exchange its last label bit over DSMEM)  */
   int passes;                /* HBM round trips per call                               */
   int row_bits;              /* two-pass: bits transformed in pass 1 (else m)          */
   int cluster;               /* CTAs per cluster in the fused (or first) pass          */

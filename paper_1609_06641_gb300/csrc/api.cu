@@ -60,7 +60,8 @@ enum Tier {
   kTierRagged = 4,
   kTierLowp = 5,
   kTierRowStack = 6,
-  kTierTmem = 7
+  kTierTmem = 7,
+  kTierTmemCross = 8
 };
 
 struct Shape {
@@ -438,6 +439,42 @@ chw_status_t launch_tmem_col_pass(chw_plan_s* p, int A, int clo, int var, const 
   return CHW_OK;
 }
 
+// Exchange scratch of the tensor-memory tier over SM pairs (m = 17): four 32 KB slots per
+// cluster, one cluster per two SMs of the device.
+size_t cross_scratch_bytes(int device) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return static_cast<size_t>(sms >= 2 ? sms / 2 : 1) << 17;
+}
+
+// Tensor-memory tier over a cluster (m = 17: two SMs per signal, each holding half of it);
+// `ws` holds at least cross_scratch_bytes().
+chw_status_t launch_tmem_cross(chw_plan_s* p, const void* in, void* out, int64_t total, const int8_t* diag_in,
+                               const int8_t* diag_out, void* ws, cudaStream_t st) {
+  const int M = p->m;
+  chw::TmemLaunchFn fn = chw::lookup_tmem_cross(M, fused_variant(p, true));
+  if (!fn) return fail(CHW_ERR_UNSUPPORTED, "no cross-SM tensor-memory kernel for m=%d", M);
+  CUtensorMap map, omap;
+  chw_status_t r = make_rows_map(&map, in, total, 14);
+  if (r != CHW_OK) return r;
+  r = make_runs_map(&omap, out, total, M - 8, 256);
+  if (r != CHW_OK) return r;
+  chw::FusedArgs a{};
+  a.out = out;
+  a.out_total = total;
+  a.end_scale = end_scale_f32(M);
+  a.diag_in = diag_in;
+  a.diag_out = diag_out;
+  a.diag_mask = (int64_t{1} << M) - 1;
+  a.status = p->d_status;
+  set_checks(&a, p, total);
+  if (ws == nullptr) return fail(CHW_ERR_INVALID_ARG, "internal: no exchange scratch");
+  a.xscratch = static_cast<uint4*>(ws);
+  a.xclusters = static_cast<int64_t>(cross_scratch_bytes(p->device) >> 17);
+  CHW_CUDA(fn(&map, &omap, a, total >> M, st));
+  return CHW_OK;
+}
+
 // Tensor-memory tier: the plan's batch, one signal per SM at a time.
 chw_status_t launch_tmem_pass(chw_plan_s* p, const void* in, void* out, int64_t total, const int8_t* diag_in,
                               const int8_t* diag_out, cudaStream_t st) {
@@ -576,6 +613,8 @@ chw_status_t run_transform(chw_plan_s* p, const void* x, void* y, int64_t batch,
       return launch_rowstack(p, x, y, batch, diag_in, diag_out, ws, p->rowstack_slots, st);
     case kTierTmem:
       return launch_tmem_pass(p, x, y, total, diag_in, diag_out, st);
+    case kTierTmemCross:
+      return launch_tmem_cross(p, x, y, total, diag_in, diag_out, ws, st);
     case kTierFused:
     case kTierCluster:
       return launch_row_pass(p, m, final_outmode(p), fused_variant(p, true), x, y, total, diag_in, diag_out, dmask,
@@ -790,6 +829,7 @@ std::vector<chw::TuneChoice> tune_candidates(int m, chw_dtype_t dtype, chw_norm_
   };
   if (m <= 17) {
     if (m <= 16 && chw::lookup_tmem(m, var_last, om) != nullptr) add(kTierTmem, m, 0);
+    if (m == 17 && om == 0 && chw::lookup_tmem_cross(m, var_last) != nullptr) add(kTierTmemCross, m, 0);
     // m = 15, 16: one SM holds the whole signal in tensor memory (92 % against 52-62 % for
     // the 2- and 4-CTA clusters and 41 % for the row-stack tier), so only the tensor-memory
     // kernel is timed; the others stay selectable by their flags
@@ -883,7 +923,7 @@ chw_status_t autotune_plan(chw_plan_s* p) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   const int64_t slots = std::min<int64_t>(sms > 0 ? sms : 1, tbatch);
   const size_t bytes = static_cast<size_t>(total) * 4;
-  const size_t ws_bytes = std::max(bytes, static_cast<size_t>(slots * n) * 4);
+  const size_t ws_bytes = std::max({bytes, static_cast<size_t>(slots * n) * 4, cross_scratch_bytes(p->device)});
   void *x = nullptr, *y = nullptr, *ws = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto release = [&] {
@@ -1065,11 +1105,17 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     p->passes = 2;
     p->row_bits = m - (m >= 23 ? (m - 17 > 6 ? m - 17 : 6) : 6);
   } else if (m == 17 && p->order == 0 && (flags & (CHW_FLAG_ROWSTACK | CHW_FLAG_CLUSTER | CHW_FLAG_TEST_STALL)) == 0) {
-    // 2^17 words do not fit one SM: the two-pass split (a = 9) measured faster on GB300
-    // than the 8-CTA cluster (3078 vs 2722 GB/s on 2048 signals)
-    p->tier = kTierTwoPass;
-    p->passes = 2;
-    p->row_bits = 8;
+    // 2^17 words do not fit one SM: two SMs hold half a signal each in tensor memory and
+    // exchange the last label bit over DSMEM (one HBM round trip); without that kernel the
+    // two-pass split (a = 9), measured faster on GB300 than the 8-CTA cluster (3078 vs
+    // 2722 GB/s on 2048 signals)
+    if (chw::lookup_tmem_cross(17, fused_variant(p, true)) != nullptr) {
+      p->tier = kTierTmemCross;
+    } else {
+      p->tier = kTierTwoPass;
+      p->passes = 2;
+      p->row_bits = 8;
+    }
   } else if (m <= 17) {
     if (m < 5 && p->total % 32 != 0) {
       p->tier = kTierSimple;
@@ -1124,8 +1170,9 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
       return fail(CHW_ERR_OOM, "workspace of %zu bytes: %s", p->workspace_bytes, cudaGetErrorString(e));
     }
   }
-  if (p->tier == kTierTwoPass) {
-    p->workspace_bytes = static_cast<size_t>(p->total) * elem_bytes(dtype);
+  if (p->tier == kTierTwoPass || p->tier == kTierTmemCross) {
+    p->workspace_bytes = p->tier == kTierTmemCross ? cross_scratch_bytes(p->device)
+                                                   : static_cast<size_t>(p->total) * elem_bytes(dtype);
     e = cudaMalloc(&p->workspace, p->workspace_bytes);
     if (e != cudaSuccess) {
       cudaFree(p->d_status);
@@ -1224,6 +1271,7 @@ chw_status_t chw_plan_get_info(chw_plan_t p, chw_plan_info_t* info) {
   info->cluster = 1;
   info->kernels_per_call = p->passes;
   if (p->tier == kTierFused || p->tier == kTierCluster) info->cluster = 1 << row_shape(p->m, p->tile_bits).cb;
+  if (p->tier == kTierTmemCross) info->cluster = 1 << (p->m - 16);
   if (p->tier == kTierTwoPass)
     info->cluster = tmem_row_pass(p, p->row_bits, p->order == 1 ? 4 : 1) ? 1 : 1 << row_shape(p->row_bits, p->tile_bits).cb;
   info->workspace_bytes = static_cast<int64_t>(p->workspace_bytes);
@@ -1299,6 +1347,7 @@ chw_status_t chw_forward_host(chw_plan_t p, const void* x_host, void* y_host, co
       if (cudaStreamCreateWithFlags(&p->h_stream[i], cudaStreamNonBlocking) != cudaSuccess ||
           cudaMalloc(&p->h_buf[i], bytes) != cudaSuccess ||
           (p->tier == kTierTwoPass && cudaMalloc(&p->h_ws[i], bytes) != cudaSuccess) ||
+          (p->tier == kTierTmemCross && cudaMalloc(&p->h_ws[i], cross_scratch_bytes(p->device)) != cudaSuccess) ||
           (p->tier == kTierRowStack &&
            cudaMalloc(&p->h_ws[i], static_cast<size_t>(p->rowstack_slots << p->m) * eb) != cudaSuccess) ||
           (lowp && (cudaMalloc(&p->h_exp[i][0], chunk * sizeof(int32_t)) != cudaSuccess ||

@@ -82,6 +82,11 @@ struct FusedArgs {
   // Haar side output (chw_forward_haar): z = Psi_m x (eq. (2)) of every signal, written
   // from the same pass at the signal's place in this array (the layout of y); nullptr: none.
   void* haar_z;
+  // Signals over a pair of SMs (tensor-memory kernel, XP = 1): the exchange scratch in
+  // global memory (L2-resident), four 32 KB slots per cluster (two per CTA, by the chunk
+  // parity), room for `xclusters` clusters; the launch keeps its grid within it.
+  uint4* xscratch;
+  int64_t xclusters;
   CUtensorMap tout;  // the type carries the alignment TMA needs
 };
 

@@ -119,5 +119,12 @@ TmemLaunchFn lookup_tmem_hz(int m, int var);
 // m = 16.  nullptr for other shapes.
 TmemLaunchFn lookup_tmem_col(int m, int clo, int var);
 
+// The tensor-memory kernel for one signal of 2^m words spread over a cluster of 2^(m-16)
+// SMs (m = 17: two), dyadic order: `tin` as for the whole-signal kernel, `tout` the output
+// as rows of 2^(m-8) words with boxes of 32 words x 256 rows (SWIZZLE_128B); `units` is the
+// number of signals.  FusedArgs::diag_mask must be 2^m - 1 when D is given.  nullptr for
+// other m.
+TmemLaunchFn lookup_tmem_cross(int m, int var);
+
 }  // namespace chw
 

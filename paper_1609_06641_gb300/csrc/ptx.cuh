@@ -170,6 +170,25 @@ __device__ __forceinline__ void st_dsmem_v4(uint32_t addr, uint32_t a, uint32_t 
                : "memory");
 }
 
+// Bulk copies between global and shared memory (no tensor map): 16-byte aligned addresses,
+// a size that is a multiple of 16 bytes.  The load counts its bytes on `bar` (complete_tx);
+// the store joins the issuing thread's bulk group (bulk_commit_group / bulk_wait_*).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+
+// Order global-memory accesses of the generic proxy against those of the async proxy (bulk
+// copies) of this thread.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
 // ---------------------------------------------------------------- tensor memory (tcgen05)
 // Tensor memory is 128 lanes x 512 columns of 32-bit cells per SM.  A warp reaches only
 // the 32 lanes 32 (warp mod 4) .. +31; with the 32x32b shape thread i of the warp reads or

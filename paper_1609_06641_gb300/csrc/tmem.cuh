@@ -28,6 +28,19 @@
 // then land on output bits M-1-b exactly as in the whole-signal case; only the run index
 // of a thread (its output bits M-8..M-1) is formed differently.
 //
+// Signals of 2^17 words (XP = 1) spread over a cluster of two CTAs, one per SM: CTA c
+// holds the 2^16 labels whose bit 16 equals c and runs label bits 0..15 exactly as above.
+// Label bit 16 pairs values held by different SMs.  For every output chunk each thread
+// keeps half of its 64 values (split by the dyadic output bit 5 of the chunk) and hands the
+// other half to the same thread of the peer CTA through an L2-resident scratch slot: the
+// CTA stages its 32 KB in shared memory and writes it with one bulk copy; while the CTA
+// transforms its next input row, one thread waits for that copy and signals the peer, and
+// another waits for the peer's signal and bulk-loads the peer's 32 KB into shared memory.
+// Then the butterflies of label bit 16 run and 64 consecutive outputs per thread leave by
+// TMA as above.  (The same exchange over distributed shared memory was measured slower on
+// GB300: its per-SM bandwidth stalls the threads that issue it.)  Every value still meets
+// label bits 0..16 in order, so the results equal the cascade's.
+//
 // Tensor memory is 128 lanes x 512 columns x 4 bytes = 256 KB per SM: one 2^16-word
 // signal.  Shared memory holds two 64 KB row buffers (the next rows' TMA loads overlap
 // the current row and the column butterflies) and a 64 KB staging buffer, which keeps one
@@ -197,8 +210,11 @@ __device__ __forceinline__ void row_phases_from(uint32_t (&v)[64], uint32_t* buf
   butterflies<P2, 5, 11>(v, bf);
 }
 
+// Two row buffers and the staging buffer, barriers and the allocation slot; a signal
+// spread over 2^XP SMs (XP > 0) adds a 32 KB receive buffer and 2 XP barriers.
+template <int XP = 0>
 constexpr int tmem_smem_bytes() {
-  return (12 << kTmemTB) + 1024 + 64;  // two row buffers and the staging buffer, barriers, slot
+  return (12 << kTmemTB) + (XP > 0 ? (2 << kTmemTB) : 0) + 1024 + (XP > 0 ? 128 : 64);
 }
 
 // Output tensor map of the kernel's TMA stores, SWIZZLE_128B, boxes 32 words wide.  Dyadic
@@ -222,7 +238,7 @@ __device__ __forceinline__ uint32_t tmem_col(uint32_t par, int r, int k) {
   }
 }
 
-template <int M, class BF, bool SCALE, int OM, int CLO = 0, bool HZ = false>
+template <int M, class BF, bool SCALE, int OM, int CLO = 0, bool HZ = false, int XP = 0>
 __global__ void __launch_bounds__(kTmemThreads, 1)
     tmem_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                 const FusedArgs args, const int64_t units) {
@@ -234,6 +250,8 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   static_assert(!HZ || (CLO == 0 && OM == 0), "side output of whole signals in dyadic order");
   constexpr int ZM = HZ ? M : 0;
   static_assert(ZM == 0 || reg_label(T::P3, 0) == 0u, "chunk 0, register 0 holds labels with bits 8..13 zero");
+  static_assert(XP == 0 || (M == 16 && OM == 0 && CLO == 0 && !HZ && XP == 1),
+                "a signal over two SMs: whole 2^17-word signals in dyadic order");
   constexpr uint32_t LMASK = (1u << TB) - 1u;
   constexpr Phase P2 = T::P2, P3 = T::P3;
   constexpr Lin LB = T::LB;
@@ -241,12 +259,22 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   uint8_t* base = align1024(smem_raw);
   uint32_t* bufs = reinterpret_cast<uint32_t*>(base);  // row buffers g mod 2
   uint32_t* stage = bufs + (2u << TB);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (1u << TB));
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint32_t* xbuf = stage + (1u << TB);  // XP > 0: 32 KB of exchanged values, [piece j][thread]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xbuf + (XP > 0 ? (1u << (TB - 1)) : 0u));
+  // XP > 0: readyb[c & 1]: the peer's values of chunk c are in its scratch slot (a remote
+  // arrival); loadb: the bulk load of the peer's values into xbuf has landed
+  uint64_t* readyb = bar + 2;
+  uint64_t* loadb = bar + 4;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 5);
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   if (tid == 0) {
     mbar_init(bar, 1);
     mbar_init(bar + 1, 1);
+    if (XP > 0) {
+      mbar_init(readyb, 1);
+      mbar_init(readyb + 1, 1);
+      mbar_init(loadb, 1);
+    }
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -257,14 +285,22 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tmem = *slot;
+  const uint32_t rank = XP > 0 ? cluster_ctarank() : 0u;
+  if constexpr (XP > 0) {
+    cluster_arrive();  // every CTA's barriers exist before a peer signals them
+    cluster_wait();
+  }
   // this thread's lane and its warp's half of the columns
   const uint32_t taddr = tmem + ((32u * (warp & 3u)) << 16) + (T::NCOLS / 2) * (warp >> 2);
 
-  const int64_t stride = gridDim.x;
-  const int64_t first = blockIdx.x;
+  const int64_t stride = gridDim.x >> XP;
+  const int64_t first = blockIdx.x >> XP;
   const int64_t K = first < units ? (units - first + stride - 1) / stride : 0;
   const int64_t G = K * R;  // rows this CTA loads
-  auto elem0 = [&](int64_t k) { return unit_elem<M>(args, args.in_off, first + k * stride); };
+  // first input element of this CTA's 2^M labels of unit k (signals of 2^(M+XP) words)
+  auto elem0 = [&](int64_t k) {
+    return unit_elem<M + XP>(args, args.in_off, first + k * stride) + (static_cast<int64_t>(rank) << M);
+  };
   auto rowe = [&](int64_t g) { return elem0(g / R) + ((g % R) << TB); };  // first element of row g
   if (tid == 0) {
     if (G > 0) tile_issue_at<TB>(&tin, rowe(0), bufs, bar, args);
@@ -283,6 +319,32 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   const uint32_t rho = CLO == 0 ? bitrev_bits(tl, 8)
                                 : ((tl & ((1u << CLO) - 1u)) << (8 - CLO)) | bitrev_bits(tl >> CLO, 8 - CLO);
   const uint32_t sxor = (rho & 7u) << 2;
+  // The exchange of a signal over two SMs (XP = 1), one chunk at a time: xn is the chunk
+  // (counted over this CTA's signals) whose exchange is under way, xstate its step --
+  // 1: this CTA's values are being written to its scratch slot; 2: the peer has been told
+  // they are there; 3: the load of the peer's values has been issued.  Every thread keeps
+  // the same xn and xstate; threads 32 and 0 carry out steps 2 and 3.
+  int64_t xn = 0;
+  int xstate = 0;
+  int64_t nload = 0;  // bulk loads issued on loadb (thread 0)
+  auto xslot = [&](uint32_t r, int64_t n) {  // scratch slot of CTA rank r for chunk n
+    return args.xscratch + ((((static_cast<int64_t>(first) * 2 + r) * 2 + (n & 1))) << 11);
+  };
+  auto signal_peer = [&]() {  // thread 32: this CTA's values of chunk xn are in L2
+    bulk_wait_all();            // the bulk store of this thread has completed
+    fence_proxy_async_global();
+    mbar_remote_arrive(readyb + (xn & 1), rank ^ 1u);
+  };
+  auto load_peer = [&]() {  // thread 0: once the peer's values are in L2, load them into xbuf
+    if (waiting && !mbar_wait_cluster_bounded(readyb + (xn & 1), static_cast<uint32_t>((xn >> 1) & 1), tries)) {
+      waiting = false;
+      atomicCAS(args.status, 0, kStatusTimeout);
+    }
+    fence_proxy_async_global();
+    mbar_arrive_expect_tx(loadb, 32u << 10);
+    bulk_load(xbuf, xslot(rank ^ 1u, xn), 32u << 10, loadb);
+    ++nload;
+  };
 
   // Row r of signal k: label bits 0..13, then into tensor memory.
   auto row = [&](int64_t k, int r) {
@@ -310,10 +372,22 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     if constexpr (!T::b_is_s) __syncthreads();
     store_phase<P2, P2, LB, LMASK>(v, buf, thread_pos<P2, LB, LMASK>(lane, warp, 0));
     __syncthreads();
+    if constexpr (XP > 0) {  // the exchange of the previous chunk advances during the row
+      if (xstate == 1) {
+        if (tid == 32) signal_peer();
+        xstate = 2;
+      }
+    }
     load_phase<P3, LB, LMASK>(v, buf, thread_pos<P3, LB, LMASK>(lane, warp, 0));
     bfly<P3, 11, TB, 0, BF, ZM, SCALE>(v, bf, lane, warp, &hz);
     __syncthreads();  // the row buffer is no longer read: refill it
     if (tid == 0 && g + 2 < G) tile_issue_at<TB>(&tin, rowe(g + 2), buf, bar + (g & 1), args);
+    if constexpr (XP > 0) {
+      if (xstate == 2) {  // (thread 32's store has completed: the barrier above orders it)
+        if (tid == 0) load_peer();
+        xstate = 3;
+      }
+    }
     const uint32_t par = static_cast<uint32_t>(k & 1);
     tmem_st16<0>(taddr + tmem_col<M>(par, r, 0), v);
     tmem_st16<16>(taddr + tmem_col<M>(par, r, 16), v);
@@ -322,9 +396,109 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     tmem_wait_st();
   };
 
+  // Label bit M (XP = 1) of output chunk q of signal k, in two steps around the next row's
+  // phases so that the exchange overlaps them.  cross_send: u holds the chunk's values with
+  // label bits 0..M-1 done; the value at dyadic position 64 q + w of the thread's run within
+  // this CTA's 2^M labels is u[src(q, w)].  The thread keeps the 32 values of the half
+  // w >> 5 = rank and writes the other half to xbuf (16-byte piece j of thread t at piece
+  // 256 j + t), which thread 32 copies to this CTA's scratch slot.  cross_finish: the peer's
+  // values of the kept half, loaded into xbuf the same way, are butterflied with the kept
+  // ones (the rank-0 CTA's value first) and stored: the thread's 64 outputs are the
+  // consecutive words
+  //   2 (rho 2^8 + 64 q + 32 rank + j) + e = rho 2^9 + 64 (2 q + rank) + 2 j + e
+  // of the signal (e = label bit M), staged and stored by TMA like the other chunks.
+  auto cross_send = [&](int64_t k, auto qq, uint32_t (&u)[64], uint32_t (&keep)[32]) {
+    constexpr int q = qq;
+    const bool hi = rank != 0;
+    uint32_t give[32];
+    sfor<32>([&](auto jj) {
+      constexpr int j = jj;
+      const uint32_t lo = u[T::src(q, j)], up = u[T::src(q, 32 + j)];
+      keep[j] = hi ? up : lo;
+      give[j] = hi ? lo : up;
+    });
+    // xbuf is free: the previous chunk's values were read before the last barrier
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      *reinterpret_cast<uint4*>(xbuf + 4u * ((j << 8) + tid)) =
+          make_uint4(give[4 * j], give[4 * j + 1], give[4 * j + 2], give[4 * j + 3]);
+    fence_proxy_async_smem();
+    __syncthreads();
+    xn = k * R + q;
+    if (tid == 32) {
+      bulk_store(xslot(rank, xn), xbuf, 32u << 10);
+      bulk_commit_group();
+    }
+    xstate = 1;
+  };
+  auto cross_finish = [&](int64_t k, auto qq, const uint32_t (&keep)[32]) {
+    constexpr int q = qq;
+    const bool hi = rank != 0;
+    if (xstate == 1) {  // no row ran since cross_send (the last signal)
+      if (tid == 32) signal_peer();
+      __syncthreads();
+      xstate = 2;
+    }
+    if (xstate == 2) {
+      if (tid == 0) load_peer();
+      xstate = 3;
+    }
+    if (waiting && !mbar_wait_bounded(loadb, static_cast<uint32_t>(xn & 1), tries)) {
+      waiting = false;
+      if (lane == 0) atomicCAS(args.status, 0, kStatusTimeout);
+    }
+    xstate = 0;
+    uint32_t v[64];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint4 t = *reinterpret_cast<const uint4*>(xbuf + 4u * ((j << 8) + tid));
+      const uint32_t g[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        uint32_t a = hi ? g[f] : keep[4 * j + f], b = hi ? keep[4 * j + f] : g[f];
+        bf(a, b);
+        v[8 * j + 2 * f] = a;
+        v[8 * j + 2 * f + 1] = b;
+      }
+    }
+    if constexpr (SCALE) {
+#pragma unroll
+      for (int i = 0; i < 64; ++i) v[i] = __float_as_uint(__fmul_rn(__uint_as_float(v[i]), args.end_scale));
+    }
+    const int64_t ob = unit_elem<M + XP>(args, args.out_off, first + k * stride);
+    const uint32_t xr = 64u * ((static_cast<uint32_t>(q) << 1) | rank);  // within the output run
+    if (args.diag_out != nullptr) {  // D acts on the stored positions
+      const int64_t at = (static_cast<int64_t>(rho) << (M + XP - 8)) + xr;
+      const int8_t* d = args.diag_out + (at & args.diag_mask);
+#pragma unroll
+      for (int i = 0; i < 64; ++i)
+        if (d[i] < 0) v[i] = std::is_same_v<BF, BfI32> ? 0u - v[i] : v[i] ^ 0x80000000u;
+    }
+    if (tid == 0) bulk_wait_read();  // the previous chunk's TMA stores have read the buffer
+    __syncthreads();                 // ... and every thread has read its values from xbuf
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const uint32_t box = static_cast<uint32_t>(c >> 3) << (TB - 1);
+      *reinterpret_cast<uint4*>(stage + box + ((rho << 5) | ((4u * (c & 7)) ^ sxor))) =
+          make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      if (args.checked && !range_ok(ob, int64_t{1} << (M + XP), args.out_total)) {
+        check_fail(args.status, ob);
+      } else {
+        const int y = static_cast<int>(ob >> (M + XP - 8));
+        tma_store_2d(&tout, stage, static_cast<int>(xr), y);
+        tma_store_2d(&tout, stage + (1u << (TB - 1)), static_cast<int>(xr) + 32, y);
+      }
+      bulk_commit_group();
+    }
+  };
+
   // Output chunk q of signal k: label bits 14..M-1 on registers [q JW, (q+1) JW) of every
   // row, staged in output order and stored by TMA.
-  auto chunk = [&](int64_t k, auto qq) {
+  auto chunk = [&](int64_t k, auto qq, uint32_t (&keep)[XP > 0 ? 32 : 1]) {
     constexpr int q = qq;
     const uint32_t par = static_cast<uint32_t>(k & 1);
     uint32_t u[64];  // u[r JW + j] = row r, register q JW + j
@@ -374,6 +548,10 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
         if constexpr (SCALE) val = __float_as_uint(__fmul_rn(__uint_as_float(val), end_scale_const(M)));
         zs[0] = val;
       }
+    }
+    if constexpr (XP > 0) {
+      cross_send(k, qq, u, keep);
+      return;
     }
     if constexpr (SCALE) {
 #pragma unroll
@@ -554,15 +732,24 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
 
   // Software pipeline: output chunk i of signal t-1 frees the tensor-memory columns that
   // row i of signal t fills, so every step reads one row and writes one chunk.
+  // With XP = 1 the chunk's exchange with the peer runs while this CTA transforms the row.
   for (int64_t t = 0; t <= K; ++t) {
 #pragma unroll 1
     for (int i = 0; i < R; ++i) {
+      uint32_t keep[XP > 0 ? 32 : 1];
       if (t >= 1) {
         sfor<R>([&](auto qq) {
-          if (static_cast<int>(qq) == i) chunk(t - 1, qq);
+          if (static_cast<int>(qq) == i) chunk(t - 1, qq, keep);
         });
       }
       if (t < K) row(t, i);
+      if constexpr (XP > 0) {
+        if (t >= 1) {
+          sfor<R>([&](auto qq) {
+            if (static_cast<int>(qq) == i) cross_finish(t - 1, qq, keep);
+          });
+        }
+      }
     }
   }
   // Leave no TMA load in flight into shared memory, even when a wait above gave up: wait
@@ -574,10 +761,19 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     }
   }
   if (tid == 0) bulk_wait_all();  // the output stores have completed
+  if constexpr (XP > 0) {
+    if (tid == 32) bulk_wait_all();  // the exchange stores too
+    // and the last load into xbuf (already waited for, unless a wait above gave up)
+    if (tid == 0 && nload > 0) mbar_wait_bounded(loadb, static_cast<uint32_t>((nload - 1) & 1), kWaitTries);
+  }
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
   if (warp == 0) tmem_dealloc(tmem, T::NCOLS);
+  if constexpr (XP > 0) {
+    cluster_arrive();  // no CTA leaves while a peer may still write into it or signal it
+    cluster_wait();
+  }
 }
 
 }  // namespace chw

@@ -59,7 +59,7 @@ def test_f32_every_m(chw, torch, m, norm):
     if m in (15, 16):
         assert info.tier == 7 and info.cluster == 1  # one CTA per signal, tensor memory
     elif m == 17:
-        assert info.tier == 3 and info.passes == 2 and info.row_bits == 8  # two passes, a = 9
+        assert info.tier == 8 and info.passes == 1 and info.cluster == 2  # two SMs, tensor memory
 
 
 @pytest.mark.parametrize("m", [15, 16, 17])

@@ -8,7 +8,7 @@ norm, order) to a choice and survives a save/load round trip through its text fi
 
 import pytest
 
-TIER_FUSED, TIER_CLUSTER, TIER_TWO_PASS, TIER_ROWSTACK, TIER_TMEM = 1, 2, 3, 6, 7
+TIER_FUSED, TIER_CLUSTER, TIER_TWO_PASS, TIER_ROWSTACK, TIER_TMEM, TIER_TMEM_CROSS = 1, 2, 3, 6, 7, 8
 
 
 @pytest.fixture(scope="module")
@@ -48,6 +48,11 @@ def test_m14_and_m17_one_pass_candidates(chw):
     assert (TIER_FUSED, 14, 14) in chw.chw_tune_candidates(14, "f32", "end")
     c17 = chw.chw_tune_candidates(17, "f32", "end")
     assert (TIER_CLUSTER, 17, 14) in c17 and all(t != TIER_ROWSTACK for t, _, _ in c17)
+    # the pair of SMs holding the signal in tensor memory: dyadic order only
+    assert (TIER_TMEM_CROSS, 17, 0) in c17
+    assert (TIER_TMEM_CROSS, 17, 0) in chw.chw_tune_candidates(17, "i32", "none")
+    for order in ("natural", "sequency"):
+        assert all(t != TIER_TMEM_CROSS for t, _, _ in chw.chw_tune_candidates(17, "f32", "end", order=order))
 
 
 @pytest.mark.parametrize("m", [17, 18, 20, 23, 24, 28, 29, 30])
