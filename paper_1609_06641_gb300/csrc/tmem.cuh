@@ -318,7 +318,12 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   // bitrev of the row's label bits CLO..7
   const uint32_t rho = CLO == 0 ? bitrev_bits(tl, 8)
                                 : ((tl & ((1u << CLO) - 1u)) << (8 - CLO)) | bitrev_bits(tl >> CLO, 8 - CLO);
-  const uint32_t sxor = (rho & 7u) << 2;
+  // staging swizzle: 16-byte piece c of run rho at piece c ^ (rho & skey) of its 128-byte
+  // row -- the TMA's 128-byte swizzle (skey = 7), or for a first pass storing blocks of 16,
+  // 8 or 4 columns by TMA, the 64-, 32-byte or no swizzle of their narrower box rows
+  // (skey = 3, 1, 0), which permute the same pieces of the same rows
+  const uint32_t skey = OM == 1 && args.tma_store ? (1u << ((args.colblock_c != 0 ? args.colblock_c : 5) - 2)) - 1u : 7u;
+  const uint32_t sxor = (rho & skey) << 2;
   // The exchange of a signal over two SMs (XP = 1), one chunk at a time: xn is the chunk
   // (counted over this CTA's signals) whose exchange is under way, xstate its step --
   // 1: this CTA's values are being written to its scratch slot; 2: the peer has been told
@@ -678,10 +683,11 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
           bulk_commit_group();
         }
       } else if (OM == 1 && args.tma_store) {
-        // Column blocks of 32: the 32-word segment g of row r (signal s) lives at
-        // s 2^(a+M) + g 2^(a+5) + 32 r.  The staged boxes hold, for every run rho, the
-        // segments g = rho 2^(M-13) + 2q + h (box h), so each box is one tensor store through
-        // the 5-D view {32 words, r, g mod 2^(M-13), rho, s} of the scratch.
+        // Column blocks of 2^c (c = 2..5): the 2^c-word segment g of row r (signal s) lives
+        // at s 2^(a+M) + g 2^(a+c) + 2^c r.  Box h of the staged chunk holds, for every run
+        // rho, the segments g = rho 2^(M-8-c) + (64 q + 32 h) / 2^c + i, i < 2^(5-c), so each
+        // box is one tensor store through the 5-D view {2^c words, r, g mod 2^(M-8-c), rho,
+        // s} of the scratch.
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -692,8 +698,9 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
             check_fail(args.status, sig0);
           } else {
             const int r = static_cast<int>(u & ((int64_t{1} << cba) - 1)), s = static_cast<int>(u >> cba);
-            tma_store_5d(&tout, stage, 0, r, 2 * q, 0, s);
-            tma_store_5d(&tout, stage + (1u << (TB - 1)), 0, r, 2 * q + 1, 0, s);
+            const int cw = args.colblock_c != 0 ? args.colblock_c : 5;
+            tma_store_5d(&tout, stage, 0, r, (64 * q) >> cw, 0, s);
+            tma_store_5d(&tout, stage + (1u << (TB - 1)), 0, r, (64 * q + 32) >> cw, 0, s);
           }
           bulk_commit_group();
         }
