@@ -164,6 +164,15 @@ struct TmemCfg {
     return true;
   }
   static_assert(OM == 2 || chunks_ok(), "each output chunk is exactly one register range of every row");
+  // Every chunk maps its registers to the same low output bits: src(q, w) = src(0, w), so
+  // the chunk epilogue of the dyadic and sequency orders may take q at run time.
+  static constexpr bool src_chunk_free() {
+    for (int q = 1; q < R; ++q)
+      for (int w = 0; w < 64; ++w)
+        if (src(q, w) != src(0, w)) return false;
+    return true;
+  }
+  static_assert(OM == 2 || src_chunk_free(), "the chunk's register map does not depend on the chunk");
 
   // Natural order: register k of row r holds output bits 8..M-1 = its label bits 8..M-1.
   // In output chunk q they are the row psi = bits M-6..M-1 (64 rows, 2^(M-6) words apart)
@@ -412,13 +421,12 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
   // consecutive words
   //   2 (rho 2^8 + 64 q + 32 rank + j) + e = rho 2^9 + 64 (2 q + rank) + 2 j + e
   // of the signal (e = label bit M), staged and stored by TMA like the other chunks.
-  auto cross_send = [&](int64_t k, auto qq, uint32_t (&u)[64], uint32_t (&keep)[32]) {
-    constexpr int q = qq;
+  auto cross_send = [&](int64_t k, int q, uint32_t (&u)[64], uint32_t (&keep)[32]) {
     const bool hi = rank != 0;
     uint32_t give[32];
     sfor<32>([&](auto jj) {
       constexpr int j = jj;
-      const uint32_t lo = u[T::src(q, j)], up = u[T::src(q, 32 + j)];
+      const uint32_t lo = u[T::src(0, j)], up = u[T::src(0, 32 + j)];
       keep[j] = hi ? up : lo;
       give[j] = hi ? lo : up;
     });
@@ -436,8 +444,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     }
     xstate = 1;
   };
-  auto cross_finish = [&](int64_t k, auto qq, const uint32_t (&keep)[32]) {
-    constexpr int q = qq;
+  auto cross_finish = [&](int64_t k, int q, const uint32_t (&keep)[32]) {
     const bool hi = rank != 0;
     if (xstate == 1) {  // no row ran since cross_send (the last signal)
       if (tid == 32) signal_peer();
@@ -503,8 +510,15 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
 
   // Output chunk q of signal k: label bits 14..M-1 on registers [q JW, (q+1) JW) of every
   // row, staged in output order and stored by TMA.
+  // qq: the chunk index, a compile-time constant (one copy of the epilogue per chunk) or,
+  // where the epilogue is long -- sequency order, the Haar side output, a signal over two
+  // SMs -- a run-time int, so that the kernel's code stays within the instruction cache
+  // (measured on GB300 at m = 16: sequency 78 -> 90 %, side output 63 -> 70 %, m = 17
+  // 62 -> 66 %; the plain dyadic kernel runs 2.7 % faster with constants).
+  constexpr bool kRunTimeChunk = OM == 3 || ZM > 0 || XP > 0;
+  static_assert(!kRunTimeChunk || OM != 2, "natural-order staging needs the chunk index at compile time");
   auto chunk = [&](int64_t k, auto qq, uint32_t (&keep)[XP > 0 ? 32 : 1]) {
-    constexpr int q = qq;
+    const int q = static_cast<int>(qq);
     const uint32_t par = static_cast<uint32_t>(k & 1);
     uint32_t u[64];  // u[r JW + j] = row r, register q JW + j
     sfor<R>([&](auto rr) {
@@ -520,9 +534,9 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     tmem_wait_ld<48>(u);
     // Haar side output of the last label bits: the labels whose bits 0..13 are zero are
     // register 0 of output chunk 0 of the thread with label 0, one per row
-    uint32_t* zs = nullptr;
-    if constexpr (ZM > 0 && q == 0) {
-      if (args.haar_z != nullptr && tl == 0u)
+    [[maybe_unused]] uint32_t* zs = nullptr;
+    if constexpr (ZM > 0) {
+      if (q == 0 && args.haar_z != nullptr && tl == 0u)
         zs = static_cast<uint32_t*>(args.haar_z) + unit_elem<M>(args, args.out_off, first + k * stride);
     }
     sfor<M - TB>([&](auto bb) {  // label bit TB + b pairs rows r and r + 2^b
@@ -533,7 +547,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
           sfor<JW>([&](auto j) { bf(u[r * JW + j], u[(r | (1 << b)) * JW + j]); });
         }
       });
-      if constexpr (ZM > 0 && q == 0) {
+      if constexpr (ZM > 0) {
         if (zs != nullptr) {  // rows with bit b set and bits below it zero: level TB + b + 1
           sfor<R>([&](auto rr) {
             constexpr int r = rr;
@@ -547,7 +561,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
         }
       }
     });
-    if constexpr (ZM > 0 && q == 0) {
+    if constexpr (ZM > 0) {
       if (zs != nullptr) {  // the approximation: label 0 after every level
         uint32_t val = u[0];
         if constexpr (SCALE) val = __float_as_uint(__fmul_rn(__uint_as_float(val), end_scale_const(M)));
@@ -555,7 +569,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       }
     }
     if constexpr (XP > 0) {
-      cross_send(k, qq, u, keep);
+      cross_send(k, q, u, keep);
       return;
     }
     if constexpr (SCALE) {
@@ -564,12 +578,13 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     }
     const int64_t ob = unit_elem<M>(args, args.out_off, first + k * stride);
     if constexpr (OM == 2) {
-      constexpr uint32_t qo = T::nat_qo(0, q * JW);
+      constexpr int qn = decltype(qq)::value;
+      constexpr uint32_t qo = T::nat_qo(0, qn * JW);
       if (args.diag_out != nullptr) {  // D acts on the stored positions
         const int8_t* d = args.diag_out + (tl & args.diag_mask);
         sfor<64>([&](auto ii) {
           constexpr int r = ii / JW, j = ii % JW;
-          constexpr int64_t o = T::nat_high(r, q * JW + j);  // output bits 8..M-1
+          constexpr int64_t o = T::nat_high(r, qn * JW + j);  // output bits 8..M-1
           if (d[o & args.diag_mask] < 0) u[ii] = std::is_same_v<BF, BfI32> ? 0u - u[ii] : u[ii] ^ 0x80000000u;
         });
       }
@@ -580,7 +595,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       const uint32_t xc = (tl >> 2) & 7u;
       sfor<64>([&](auto ii) {
         constexpr int r = ii / JW, j = ii % JW;
-        constexpr uint32_t psi = T::nat_psi(r, q * JW + j);
+        constexpr uint32_t psi = T::nat_psi(r, qn * JW + j);
         sb[(psi << 5) | ((xc ^ (psi & 7u)) << 2)] = u[ii];
       });
       fence_proxy_async_smem();
@@ -606,7 +621,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       // parity, run pair} of the output, like the other orders, off the SM's store path.
       constexpr uint32_t L = M - 8;
       constexpr uint32_t qmask = (1u << (L - 6)) - 1u;
-      constexpr uint32_t gq = gray_inverse(q), pq = parity_of(q);
+      const uint32_t gq = gray_inverse(static_cast<uint32_t>(q)), pq = parity_of(static_cast<uint32_t>(q));
       const uint32_t dr = gray_inverse(rho);
       const uint32_t pd = dr & 1u, zr = dr >> 1, zx = zr & 7u;
       const uint32_t fx = pq ^ pd;                 // complement inside the segment
@@ -616,8 +631,8 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       uint32_t* srow = stage + (pd << (TB - 2)) + (zr << 5);
       sfor<16>([&](auto cc) {
         constexpr int c = cc;
-        constexpr int s0 = T::src(q, 4 * c), s1 = T::src(q, 4 * c + 1);
-        constexpr int s2 = T::src(q, 4 * c + 2), s3 = T::src(q, 4 * c + 3);
+        constexpr int s0 = T::src(0, 4 * c), s1 = T::src(0, 4 * c + 1);
+        constexpr int s2 = T::src(0, 4 * c + 2), s3 = T::src(0, 4 * c + 3);
         constexpr uint32_t gc = gray_inverse(c), pc = parity_of(c);
         const uint32_t C = gc ^ (fx ? 15u : 0u);
         uint4 val = (pc ^ fx) ? make_uint4(u[s2], u[s3], u[s1], u[s0]) : make_uint4(u[s0], u[s1], u[s3], u[s2]);
@@ -653,7 +668,7 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
         const int8_t* d = args.diag_out + (at & args.diag_mask);
         sfor<64>([&](auto ww) {
           constexpr int w = ww;
-          constexpr int si = T::src(q, w);
+          constexpr int si = T::src(0, w);
           if (d[64 * q + w] < 0) u[si] = std::is_same_v<BF, BfI32> ? 0u - u[si] : u[si] ^ 0x80000000u;
         });
       }
@@ -663,8 +678,8 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       // XOR rho mod 8 (the TMA's 128-byte swizzle).
       sfor<16>([&](auto cc) {
         constexpr int c = cc;
-        constexpr int s0 = T::src(q, 4 * c), s1 = T::src(q, 4 * c + 1);
-        constexpr int s2 = T::src(q, 4 * c + 2), s3 = T::src(q, 4 * c + 3);
+        constexpr int s0 = T::src(0, 4 * c), s1 = T::src(0, 4 * c + 1);
+        constexpr int s2 = T::src(0, 4 * c + 2), s3 = T::src(0, 4 * c + 3);
         constexpr uint32_t box = (c >> 3) << (TB - 1);
         *reinterpret_cast<uint4*>(stage + box + ((rho << 5) | ((4u * (c & 7)) ^ sxor))) =
             make_uint4(u[s0], u[s1], u[s2], u[s3]);
@@ -745,17 +760,17 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     for (int i = 0; i < R; ++i) {
       uint32_t keep[XP > 0 ? 32 : 1];
       if (t >= 1) {
-        sfor<R>([&](auto qq) {
-          if (static_cast<int>(qq) == i) chunk(t - 1, qq, keep);
-        });
+        if constexpr (kRunTimeChunk) {
+          chunk(t - 1, i, keep);
+        } else {
+          sfor<R>([&](auto qq) {
+            if (static_cast<int>(qq) == i) chunk(t - 1, qq, keep);
+          });
+        }
       }
       if (t < K) row(t, i);
       if constexpr (XP > 0) {
-        if (t >= 1) {
-          sfor<R>([&](auto qq) {
-            if (static_cast<int>(qq) == i) cross_finish(t - 1, qq, keep);
-          });
-        }
+        if (t >= 1) cross_finish(t - 1, i, keep);
       }
     }
   }

@@ -140,3 +140,33 @@ def test_two_pass_with_tensor_memory_rows(chw, m, b, dtype, norm):
     x = _x(m, batch, dtype, 9200 + m)
     y = _forward(chw, p, x)
     assert_bitwise(y[1:], O.chw_cascade(x[1:], m, ORACLE_DT[dtype], norm), f"m={m} b={b} {dtype} {norm}")
+
+
+@pytest.mark.parametrize("m", [28, 29])
+def test_dense_narrow_column_blocks_equal_cluster_rows(chw, m):
+    # The default split writes blocks of 2^(16 - a) columns (m = 28: 16, m = 29: 8) by TMA
+    # tensor stores; every split rounds identically, so the split with 2^17-word cluster
+    # rows in the first pass (its own store path, 32-column blocks), forced through the
+    # cache, must give the same bits on a dense signal.
+    import torch
+
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(W.uniform_pm1_f32(m, 1, seed=5)).to(dev)
+    y = torch.empty_like(x)
+    p = chw.chw_plan(m, 1, "f32", "per_level")
+    assert chw.chw_plan_get_info(p).row_bits == 16
+    chw.chw_forward(p, x, y)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(p) == 0
+    p.close()
+    choice = (3, 17, 14)  # two passes, b = 17 (8-CTA cluster rows), 2^14-word tiles
+    assert choice in chw.chw_tune_candidates(m, "f32", "per_level")
+    chw.chw_tune_cache_put(torch.cuda.get_device_name(0), m, 1, "f32", "per_level", choice, 1.0)
+    q = chw.chw_plan(m, 1, "f32", "per_level", chw.CHW_FLAG_AUTOTUNE)
+    info = chw.chw_plan_get_info(q)
+    assert (info.tier, info.row_bits, info.tile_bits) == choice and info.tuned == 2
+    y2 = torch.empty_like(x)
+    chw.chw_forward(q, x, y2)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(q) == 0
+    assert torch.equal(y.view(torch.int32), y2.view(torch.int32))
