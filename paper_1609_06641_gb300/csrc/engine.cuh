@@ -364,7 +364,10 @@ struct BfF32Plain {
 // (a, b) -> ((a+b) c, (a-b) c), each operation rounded to nearest even.  The packed form
 // adds and subtracts with f32x2 but multiplies with scalar mul.rn: a packed multiply feeding
 // the next level's packed add was observed to be fused into one FMA by the assembler (a
-// GB300 probe of chained levels), which would round differently from the cascade.
+// GB300 probe of chained levels), which would round differently from the cascade; built
+// with -fmad=false (no contraction at all) the packed mul.rn still gave results differing
+// from the cascade by a few ulps on most outputs (m = 17), while packed add and subtract
+// are exact.
 struct BfF32PerLevel {
   static constexpr bool kPacked = true;
   float c;
