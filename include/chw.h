@@ -169,15 +169,19 @@ chw_status_t chw_plan(chw_plan_t* plan, int m, int64_t batch, chw_dtype_t dtype,
  * chw_plan_ragged -- prepare one call over `count` signals of uneven lengths 2^{ms[i]}
  * (the transform of eq. (1) applied to each signal independently).
  *   ms_host   host array of `count` bit counts, each in 0..20.  The signals are packed
- *             in that order, each starting on a 32-element (128-byte) boundary:
- *             offset[0] = 0, offset[i+1] = round_up(offset[i] + 2^{ms[i]}, 32); signals
- *             with m >= 5 therefore pack back to back (chw_ragged_offsets() returns the
- *             offsets; the padding elements are neither read into results nor written).
+ *             in that order, each starting on a 32-element (128-byte) boundary, and a
+ *             signal with 15 <= m <= 17 on a multiple of 2^{m-8} elements:
+ *             e[0] = 0, offset[i] = round_up(e[i], a(ms[i])), e[i+1] =
+ *             round_up(offset[i] + 2^{ms[i]}, 32), a(m) = 2^{m-8} for m = 15..17, else 32;
+ *             the total is e[count] (chw_ragged_offsets() returns the offsets; the
+ *             padding elements are neither read into results nor written).
  *   dtype     CHW_F32 or CHW_I32 (with norm as for chw_plan).
  * The plan sorts the signals by length once and records one launch per length present
  * (signals up to 2^12 share one persistent kernel over a work list; 2^13..2^17 run as
- * batched one-pass launches and 2^18..2^20 as two-pass launches, reading and writing each
- * signal at its own offset); chw_forward_ragged() replays them as one CUDA graph launch.
+ * batched one-pass launches -- 2^15..2^17 on the tensor-memory tiers when every offset of
+ * that length is aligned as above, else on clusters of shared-memory tiles -- and
+ * 2^18..2^20 as two-pass launches, reading and writing each signal at its own offset);
+ * chw_forward_ragged() replays them as one CUDA graph launch.
  * chw_plan_get_info() reports the kernels in the graph (kernels_per_call).  With
  * CHW_FLAG_AUTOTUNE each length's configuration is timed and chosen when the plan is made
  * (tuned = 1 in chw_plan_get_info).

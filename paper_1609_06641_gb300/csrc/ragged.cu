@@ -22,6 +22,7 @@ struct RaggedGroup {
   int64_t count = 0;
   int64_t* d_off = nullptr;  // the group's signal offsets (device)
   int opt = 0;               // the group's configuration (see group_options)
+  bool aligned = false;      // every offset is a multiple of ragged_align(m)
 };
 
 struct RaggedPlan {
@@ -42,6 +43,8 @@ struct RaggedPlan {
   std::vector<RaggedGroup> groups;
   uint32_t* d_scratch = nullptr;
   int64_t scratch_words = 0;
+  uint4* d_xscratch = nullptr;  // exchange slots of the m = 17 pair kernel
+  int64_t xclusters = 0;
   int launches = 0;
   bool tuned = false;
   cudaStream_t cap = nullptr;
@@ -61,10 +64,11 @@ void free_plan(RaggedPlan* r) {
   cudaFree(r->d_off);
   for (RaggedGroup& g : r->groups) cudaFree(g.d_off);
   cudaFree(r->d_scratch);
+  cudaFree(r->d_xscratch);
   delete r;
 }
 
-bool encode_rows(CUtensorMap* map, const void* ptr, int64_t words) {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q{};
@@ -73,6 +77,11 @@ bool encode_rows(CUtensorMap* map, const void* ptr, int64_t words) {
       return nullptr;
     return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   }();
+  return enc;
+}
+
+bool encode_rows(CUtensorMap* map, const void* ptr, int64_t words) {
+  auto enc = tensor_map_encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {32, static_cast<cuuint64_t>(words / 32)};
   cuuint64_t strides[1] = {128};
@@ -88,18 +97,51 @@ float end_scale_host(int m) {  // fp32(2^{-m/2}), as the kernels compute it
   return std::ldexp(r, -(m / 2));
 }
 
-// Configurations of a length group (RaggedGroup::opt); option 0 is the built-in choice.
+// Configurations of a length group (RaggedGroup::opt).
 //   m = 13, 14   one: the batched single-CTA kernel.
-//   m = 15, 16   0: clusters of 2^14-word tiles; 1: clusters of 2^13-word tiles.
-//   m = 17       0: 8-CTA cluster; 1: the two-pass split with a = 9.
+//   m = 15, 16   0: clusters of 2^14-word tiles; 1: clusters of 2^13-word tiles; 2 (aligned
+//                groups only, the built-in choice there): one signal per SM in tensor memory.
+//   m = 17       0: 8-CTA cluster; 1: the two-pass split with a = 9; 2 (aligned groups only,
+//                the built-in choice there): a pair of SMs per signal in tensor memory.
 //   m = 18..20   the two-pass split with a = 9 (0), 8 (1) or 10 (2) column bits.
-int group_options(int m) {
-  if (m == 15 || m == 16 || m == 17) return 2;
+// The tensor-memory kernels store each signal's output by TMA as runs of 2^(m-8) words, so
+// they need offsets that are multiples of that (ragged_align); the library's packing gives
+// them, caller offsets may.
+int group_options(int m, bool aligned) {
+  if (m == 15 || m == 16 || m == 17) return aligned ? 3 : 2;
   if (m >= 18) return 3;
   return 1;
 }
 
+int default_option(int m, bool aligned) { return aligned && m >= 15 && m <= 17 ? 2 : 0; }
+
+bool tmem_opt(int m, int opt) { return m >= 15 && m <= 17 && opt == 2; }
+
 bool two_pass_opt(int m, int opt) { return m >= 18 || (m == 17 && opt == 1); }
+
+// Exchange slots of the m = 17 pair kernel: four 32 KB slots per cluster, one cluster per
+// two SMs.
+int64_t cross_clusters() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms >= 2 ? sms / 2 : 1;
+}
+
+// The output of a tensor-memory launch over the whole packed array: rows of 2^(m-8) words,
+// boxes of 32 words x 256 rows (one signal), SWIZZLE_128B.  Rows past the last whole one
+// hold no aligned signal's output.
+bool encode_runs(CUtensorMap* map, void* ptr, int64_t words, int m) {
+  auto enc = tensor_map_encoder();
+  if (!enc || (words >> (m - 8)) < 256) return false;
+  cuuint64_t dims[2] = {cuuint64_t{1} << (m - 8), static_cast<cuuint64_t>(words >> (m - 8))};
+  cuuint64_t strides[1] = {cuuint64_t{4} << (m - 8)};
+  cuuint32_t box[2] = {32, 256};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
 
 int two_pass_a(int m, int opt) {
   if (m == 17) return 9;
@@ -117,6 +159,31 @@ int group_launches(const RaggedGroup& g) {
 cudaError_t launch_group(const RaggedPlan* r, const RaggedGroup& g, int64_t count, const CUtensorMap& tx,
                          const CUtensorMap& ts, void* y, cudaStream_t st) {
   const int m = g.m;
+  if (tmem_opt(m, g.opt)) {
+    // one signal per SM (m = 15, 16) or per pair of SMs (m = 17) in tensor memory, each
+    // signal read and written at its own (aligned) offset
+    if (!g.aligned) return cudaErrorInvalidValue;
+    TmemLaunchFn fn = m == 17 ? lookup_tmem_cross(17, r->variant) : lookup_tmem(m, r->variant, 0);
+    CUtensorMap tout;
+    if (!fn || !encode_runs(&tout, y, r->total, m)) return cudaErrorInvalidValue;
+    FusedArgs a{};
+    a.status = r->d_status;
+    a.checked = r->checked;
+    a.in_total = r->total;
+    a.out = y;
+    a.out_total = r->total;
+    a.end_scale = end_scale_host(m);
+    a.diag_mask = (int64_t{1} << m) - 1;
+    a.in_off = g.d_off;
+    a.out_off = g.d_off;
+    a.sig_shift = 0;
+    if (m == 17) {
+      if (r->d_xscratch == nullptr) return cudaErrorInvalidValue;
+      a.xscratch = r->d_xscratch;
+      a.xclusters = r->xclusters;
+    }
+    return fn(&tx, &tout, a, count, st);
+  }
   if (!two_pass_opt(m, g.opt)) {
     const int tb = m == 13 ? 13 : ((m == 15 || m == 16) && g.opt == 1 ? 13 : 14);
     const int cb = m - tb > 0 ? m - tb : 0;
@@ -191,7 +258,7 @@ void tune_groups(RaggedPlan* r) {
     const int64_t sw = r->d_scratch != nullptr ? r->scratch_words : r->total;
     if (encode_rows(&tx, x, r->total) && encode_rows(&ts, sp, sw)) {
       for (RaggedGroup& g : r->groups) {
-        const int nopt = group_options(g.m);
+        const int nopt = group_options(g.m, g.aligned);
         if (nopt < 2) continue;
         const int64_t cnt = std::min<int64_t>(g.count, std::max<int64_t>(1, (int64_t{1} << 26) >> g.m));
         int best = 0;
@@ -226,12 +293,16 @@ void tune_groups(RaggedPlan* r) {
 
 }  // namespace
 
+int64_t ragged_align(int m) { return m >= 15 && m <= 17 ? int64_t{1} << (m - 8) : 32; }
+
 void ragged_pack(const uint8_t* ms, int64_t count, int64_t* off) {
   int64_t o = 0;
   for (int64_t i = 0; i < count; ++i) {
+    const int64_t al = ragged_align(ms[i]);  // 128 bytes, or a whole output run (m = 15..17)
+    o = (o + al - 1) & ~(al - 1);
     off[i] = o;
     o += int64_t{1} << ms[i];
-    o = (o + 31) & ~int64_t{31};  // every signal starts on a 128-byte boundary
+    o = (o + 31) & ~int64_t{31};
   }
   off[count] = o;
 }
@@ -284,6 +355,13 @@ RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t 
     RaggedGroup g;
     g.m = m;
     g.count = static_cast<int64_t>(go.size());
+    g.aligned = std::all_of(go.begin(), go.end(), [&](int64_t o) { return o % ragged_align(m) == 0; }) &&
+                (total >> (m - 8)) >= 256;
+    g.opt = default_option(m, g.aligned);
+    if (m == 17 && g.aligned && r->d_xscratch == nullptr && e == cudaSuccess) {
+      r->xclusters = cross_clusters();
+      e = cudaMalloc(&r->d_xscratch, static_cast<size_t>(r->xclusters) << 17);
+    }
     e = cudaMalloc(&g.d_off, go.size() * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMemcpy(g.d_off, go.data(), go.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     r->groups.push_back(g);

@@ -52,6 +52,9 @@ struct RaggedPlan;
 RaggedPlan* ragged_create(const uint8_t* ms, int64_t count, int variant, int* d_status, bool tune, std::string* why);
 // The library's packing of `count` signals: offsets[i] (count + 1 entries, the last one the
 // total), each signal starting on a 32-element (128-byte) boundary.
+// Start alignment (elements) of a signal of 2^m words in the library's packing: a whole
+// output run of the tensor-memory kernels, 2^(m-8), for m = 15..17; 32 (128 bytes) else.
+int64_t ragged_align(int m);
 void ragged_pack(const uint8_t* ms, int64_t count, int64_t* offsets);
 // The same over caller-chosen offsets (elements of x and y; `total` = their length): signals
 // with m >= 13 must start on a 32-element boundary, shorter ones anywhere.  `checked`: the

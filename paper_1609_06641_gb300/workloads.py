@@ -73,10 +73,13 @@ def ragged_ms(count, seed, lo=6, hi=20):
 
 
 def ragged_offsets(ms):
-    """Packing of a ragged batch: signal i starts at offsets[i], a multiple of 32 elements."""
+    """Packing of a ragged batch (the library's): signal i starts at offsets[i], a multiple
+    of 32 elements, or of 2^(m-8) for m = 15..17; the end is rounded up to 32."""
     off = np.zeros(len(ms) + 1, dtype=np.int64)
     o = 0
     for i, m in enumerate(ms):
+        al = 1 << (int(m) - 8) if 15 <= int(m) <= 17 else 32
+        o = (o + al - 1) // al * al
         off[i] = o
         o += 1 << int(m)
         o = (o + 31) // 32 * 32

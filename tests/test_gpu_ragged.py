@@ -107,3 +107,33 @@ def test_ragged_config_10000_signals(chw):
         assert_bitwise(got[off[i]: off[i] + ref.size], ref, f"signal {i} m={ms[i]}")
         err = O.rel_err_per_signal(got[off[i]: off[i] + ref.size], O.wht_fast_dyadic(seg.astype(np.float64), int(ms[i])))
         assert err.max() <= 1e-6
+
+
+@pytest.mark.parametrize("shift", [0, 32])
+def test_ragged_tensor_memory_groups_with_caller_offsets(chw, shift):
+    # Signals of 2^15..2^17 run on the tensor-memory tiers (one SM, or a pair of SMs for
+    # 2^17) when every offset of their length is a whole output run (2^(m-8) elements);
+    # offsets moved by 32 elements are not, and those lengths fall back to clusters of
+    # shared-memory tiles.  Both must give the cascade's bits, in every normalisation.
+    import torch
+
+    rng = np.random.default_rng(14 + shift)
+    ms = np.concatenate([np.full(5, 15), np.full(5, 16), np.full(5, 17), rng.integers(6, 15, 10)]).astype(np.uint8)
+    rng.shuffle(ms)
+    base = W.ragged_offsets(ms)
+    off = base[:-1] + shift
+    total = int(base[-1]) + shift
+    x = np.zeros(total, dtype=np.float32)
+    for i, m in enumerate(ms):
+        x[off[i]: off[i] + (1 << int(m))] = rng.standard_normal(1 << int(m), dtype=np.float32)
+    for norm in ("end", "per_level"):
+        p = chw.chw_plan_ragged(ms, "f32", norm, offsets=off, total=total)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.zeros_like(xd)
+        chw.chw_forward_ragged(p, xd, yd)
+        torch.cuda.synchronize()
+        assert chw.chw_last_device_status(p) == 0
+        got = yd.cpu().numpy()
+        for i, m in enumerate(ms):
+            ref = O.chw_cascade(x[off[i]: off[i] + (1 << int(m))][None, :], int(m), np.float32, norm)[0]
+            assert_bitwise(got[off[i]: off[i] + ref.size], ref, f"shift {shift} signal {i} m={m} {norm}")

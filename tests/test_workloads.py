@@ -44,3 +44,19 @@ def test_ragged_packing():
 def test_diag():
     d = W.diag_pm1(10, 6)
     assert d.dtype == np.int8 and set(np.unique(d)) == {-1, 1}
+
+
+def test_ragged_packing_aligns_long_signals():
+    # signals of 2^15..2^17 start on whole output runs of the tensor-memory kernels
+    # (2^(m-8) elements), every other one on 32; signals never overlap
+
+    ms, _ = W.ragged_ms(2000, 5, lo=6, hi=20)
+    off = W.ragged_offsets(ms)
+    for i, m in enumerate(ms):
+        al = 1 << (int(m) - 8) if 15 <= int(m) <= 17 else 32
+        assert off[i] % al == 0
+        assert off[i] + (1 << int(m)) <= off[i + 1]
+    assert off[-1] % 32 == 0
+    # the padding stays small: under 0.1 % of the elements for this length mix
+    assert off[-1] - sum(1 << int(m) for m in ms) < 1e-3 * off[-1]
+    assert np.all(np.diff(off) > 0)
