@@ -48,6 +48,8 @@ struct RaggedPlan {
   int launches = 0;
   bool tuned = false;
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;  // second branch of the recorded graph
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraphExec_t exec = nullptr;
   const void* gx = nullptr;
   void* gy = nullptr;
@@ -58,6 +60,9 @@ namespace {
 void free_plan(RaggedPlan* r) {
   if (r->exec) cudaGraphExecDestroy(r->exec);
   if (r->cap) cudaStreamDestroy(r->cap);
+  if (r->side) cudaStreamDestroy(r->side);
+  if (r->fork) cudaEventDestroy(r->fork);
+  if (r->join) cudaEventDestroy(r->join);
   cudaFree(r->d_tasks);
   cudaFree(r->d_head);
   cudaFree(r->d_ms);
@@ -380,6 +385,9 @@ RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t 
   }
   if (e == cudaSuccess && r->scratch_words > 0) e = cudaMalloc(&r->d_scratch, r->scratch_words * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     *why = cudaGetErrorString(e);
     cudaGetLastError();
@@ -439,17 +447,27 @@ int ragged_run(RaggedPlan* r, const void* x, void* y, cudaStream_t st, std::stri
     cudaError_t e = cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal);
     cudaError_t le = cudaSuccess;
     if (e == cudaSuccess) {
-      if (r->ntasks > 0) {
-        cudaMemsetAsync(r->d_head, 0, sizeof(int32_t), r->cap);
+      // Two branches: the two-pass groups, which share one scratch, one after another on
+      // the capture stream; the short signals and the one-pass groups on the side stream.
+      // Every launch writes its own signals only, so the branches may overlap on the GPU
+      // (each branch's kernels fill the SMs the other's tails leave idle).
+      if (cudaEventRecord(r->fork, r->cap) != cudaSuccess || cudaStreamWaitEvent(r->side, r->fork, 0) != cudaSuccess)
+        le = cudaErrorUnknown;
+      if (le == cudaSuccess && r->ntasks > 0) {
+        cudaMemsetAsync(r->d_head, 0, sizeof(int32_t), r->side);
         switch (r->variant) {
-          case kVarPerLevel: le = launch_ragged_small<kVarPerLevel>(a, r->cap); break;
-          case kVarEnd: le = launch_ragged_small<kVarEnd>(a, r->cap); break;
-          case kVarPlain: le = launch_ragged_small<kVarPlain>(a, r->cap); break;
-          default: le = launch_ragged_small<kVarI32>(a, r->cap); break;
+          case kVarPerLevel: le = launch_ragged_small<kVarPerLevel>(a, r->side); break;
+          case kVarEnd: le = launch_ragged_small<kVarEnd>(a, r->side); break;
+          case kVarPlain: le = launch_ragged_small<kVarPlain>(a, r->side); break;
+          default: le = launch_ragged_small<kVarI32>(a, r->side); break;
         }
       }
       for (const RaggedGroup& grp : r->groups)
-        if (le == cudaSuccess) le = launch_group(r, grp, grp.count, tx, ts, y, r->cap);
+        if (le == cudaSuccess && !two_pass_opt(grp.m, grp.opt)) le = launch_group(r, grp, grp.count, tx, ts, y, r->side);
+      for (const RaggedGroup& grp : r->groups)
+        if (le == cudaSuccess && two_pass_opt(grp.m, grp.opt)) le = launch_group(r, grp, grp.count, tx, ts, y, r->cap);
+      if (cudaEventRecord(r->join, r->side) != cudaSuccess || cudaStreamWaitEvent(r->cap, r->join, 0) != cudaSuccess)
+        if (le == cudaSuccess) le = cudaErrorUnknown;
       e = cudaStreamEndCapture(r->cap, &g);
       if (e == cudaSuccess && le != cudaSuccess) e = le;
     }
