@@ -267,6 +267,9 @@ struct chw_plan_s {
   chw::RaggedPlan* hw = nullptr;  // only for tiny totals that are not whole 32-word rows
   bool hw_ready = false;
   chw_plan_s* hw_big[CHW_MAX_M] = {};
+  // the scale launches of one call run on branches forked from the caller's stream
+  cudaStream_t hw_side[2] = {};
+  cudaEvent_t hw_ev[3] = {};
   // chw_forward_haar: the Haar side output of the current call (fused tiers only), else null
   void* call_haar_z = nullptr;
 };
@@ -672,6 +675,16 @@ chw_status_t build_haar_walsh(chw_plan_s* p) {
       chw_status_t r = chw_plan(&p->hw_big[k], k, 1, p->dtype, p->norm, 0);
       if (r != CHW_OK) return r;
     }
+    for (int i = 0; i < 2; ++i)
+      if (cudaStreamCreateWithFlags(&p->hw_side[i], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CHW_ERR_CUDA, "Haar-Walsh branch streams");
+      }
+    for (int i = 0; i < 3; ++i)
+      if (cudaEventCreateWithFlags(&p->hw_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CHW_ERR_CUDA, "Haar-Walsh branch events");
+      }
     p->hw_ready = true;
     return CHW_OK;
   }
@@ -738,21 +751,30 @@ chw_status_t run_haar_walsh(chw_plan_s* p, const void* z, void* y, cudaStream_t 
   if (m <= 14) {
     const Shape s = row_shape(m);
     const int64_t tile = int64_t{1} << s.tb;
-    r = launch_units(p, m, 6, vh, z, y, total, (total + tile - 1) / tile, 0, 0, 1.0f, head_end, st);
-  } else {
-    r = launch_units(p, 14, 6, vh, z, y, total, p->batch, n, 0, 1.0f, head_end, st);
+    return launch_units(p, m, 6, vh, z, y, total, (total + tile - 1) / tile, 0, 0, 1.0f, head_end, st);
   }
-  if (r != CHW_OK) return r;
-  for (int k = 14; k < m && k <= 17; ++k) {
+  // The head and the scales 2^14..2^17 read and write disjoint parts of every signal, so
+  // they run as parallel branches (the caller's stream and two forked streams, joined
+  // again before the call returns its work to the caller's stream): one launch's ramp-down
+  // leaves SMs to the others.
+  CHW_CUDA(cudaEventRecord(p->hw_ev[0], st));
+  for (cudaStream_t h : p->hw_side) CHW_CUDA(cudaStreamWaitEvent(h, p->hw_ev[0], 0));
+  r = launch_units(p, 14, 6, vh, z, y, total, p->batch, n, 0, 1.0f, head_end, p->hw_side[0]);
+  for (int k = 14; k < m && k <= 17 && r == CHW_OK; ++k) {
+    cudaStream_t bs = k == 14 ? p->hw_side[1] : (k == 15 ? p->hw_side[0] : st);
     if (k == 15 || k == 16) {
       r = launch_tmem_units(p, k, 0, fused_variant(p, true), z, y, total, p->batch, n, int64_t{1} << k, nullptr,
-                            nullptr, end_scale_f32(k), st);
+                            nullptr, end_scale_f32(k), bs);
     } else {
       r = launch_units(p, k, 0, fused_variant(p, true), z, y, total, p->batch, n, int64_t{1} << k, end_scale_f32(k),
-                       0, st);
+                       0, bs);
     }
-    if (r != CHW_OK) return r;
   }
+  for (int i = 0; i < 2; ++i) {  // join the branches (also after a failed launch)
+    CHW_CUDA(cudaEventRecord(p->hw_ev[1 + i], p->hw_side[i]));
+    CHW_CUDA(cudaStreamWaitEvent(st, p->hw_ev[1 + i], 0));
+  }
+  if (r != CHW_OK) return r;
   for (int k = 18; k < m; ++k) {
     chw_plan_s* b = p->hw_big[k];
     for (int64_t s = 0; s < p->batch; ++s) {
@@ -1218,6 +1240,10 @@ chw_status_t chw_plan_destroy(chw_plan_t p) {
   if (p->hw) chw::ragged_destroy(p->hw);
   for (chw_plan_s* b : p->hw_big)
     if (b) chw_plan_destroy(b);
+  for (cudaStream_t h : p->hw_side)
+    if (h) cudaStreamDestroy(h);
+  for (cudaEvent_t h : p->hw_ev)
+    if (h) cudaEventDestroy(h);
   delete p;
   return CHW_OK;
 }
