@@ -629,10 +629,29 @@ constexpr bool z_v4_ok(const Phase& p) {
   for (int i = 0; i < p.ncta; ++i) tb |= 1u << p.cta[i];
   return ((tb >> (T + 1)) & 3u) == 0u && ZM - T - 1 >= 2;
 }
+// The same for eight consecutive positions (one 32-byte store).
+template <int T, int ZM>
+constexpr bool z_v8_ok(const Phase& p) {
+  if (T >= ZM) return false;
+  uint32_t tb = 0;
+  for (int i = 0; i < 5; ++i) tb |= 1u << p.lane[i];
+  for (int i = 0; i < p.nwarp; ++i) tb |= 1u << p.warp[i];
+  for (int i = 0; i < p.ncta; ++i) tb |= 1u << p.cta[i];
+  return ((tb >> (T + 1)) & 7u) == 0u && ZM - T - 1 >= 3;
+}
+// All eight positions from `at` (a multiple of 8) are captured in registers.
+template <int T, int ZM>
+constexpr bool z_full8(const Phase& p, uint32_t at) {
+  for (uint32_t i = 0; i < 8; ++i)
+    if (z_reg_at<T, ZM>(p, at | i) < 0) return false;
+  return true;
+}
 
 // The captures after the butterflies of label bit T (T == ZM: the approximation, after the
-// last bit) for signals of 2^ZM labels; tl = the thread's label bits (with hz.hi).  Four
-// captures at consecutive z positions leave as one 16-byte store where the layout allows.
+// last bit) for signals of 2^ZM labels; tl = the thread's label bits (with hz.hi).  Eight
+// (four) captures at consecutive z positions leave as one 32-byte (16-byte) store where
+// the layout allows; the 32-byte stores need z on a 32-byte boundary, else two 16-byte
+// stores are issued.
 template <Phase P, int T, int ZM, bool ZEND>
 __device__ __forceinline__ void haar_capture(const uint32_t (&v)[64], uint32_t tl, const HaarZ& hz) {
   constexpr uint32_t smask = (1u << ZM) - 1u;
@@ -641,6 +660,8 @@ __device__ __forceinline__ void haar_capture(const uint32_t (&v)[64], uint32_t t
   const uint32_t tpart = ((tl >> ZM) << ZM) + (T < ZM ? ((tl & smask) >> (T + 1)) : 0u);
   constexpr float sc = end_scale_const(T < ZM ? T + 1 : ZM);
   constexpr bool V4 = z_v4_ok<T, ZM>(P);
+  constexpr bool V8 = z_v8_ok<T, ZM>(P);
+  const bool a32 = (reinterpret_cast<uintptr_t>(hz.z) & 31u) == 0u;
   auto scaled = [&](uint32_t x) {
     if constexpr (ZEND) x = __float_as_uint(__fmul_rn(__uint_as_float(x), sc));
     return x;
@@ -649,6 +670,32 @@ __device__ __forceinline__ void haar_capture(const uint32_t (&v)[64], uint32_t t
     constexpr int k = kk;
     if constexpr (z_hit<T, ZM>(P, k)) {
       constexpr uint32_t rp = z_rpart<T, ZM>(P, k);
+      constexpr bool in8 = V8 && z_full8<T, ZM>(P, rp & ~7u);  // part of a complete group of eight
+      if constexpr (in8) {
+        if constexpr ((rp & 7u) == 0u) {
+          constexpr int r1 = z_reg_at<T, ZM>(P, rp | 1u), r2 = z_reg_at<T, ZM>(P, rp | 2u),
+                        r3 = z_reg_at<T, ZM>(P, rp | 3u), r4 = z_reg_at<T, ZM>(P, rp | 4u),
+                        r5 = z_reg_at<T, ZM>(P, rp | 5u), r6 = z_reg_at<T, ZM>(P, rp | 6u),
+                        r7 = z_reg_at<T, ZM>(P, rp | 7u);
+          const uint32_t at = tpart + rp;
+          if (at + 7u < hz.limit) {
+            if (a32) {
+              st_global_v8(hz.z + at, scaled(v[k]), scaled(v[r1]), scaled(v[r2]), scaled(v[r3]), scaled(v[r4]),
+                           scaled(v[r5]), scaled(v[r6]), scaled(v[r7]));
+            } else {
+              st_global_v4(hz.z + at, scaled(v[k]), scaled(v[r1]), scaled(v[r2]), scaled(v[r3]));
+              st_global_v4(hz.z + at + 4u, scaled(v[r4]), scaled(v[r5]), scaled(v[r6]), scaled(v[r7]));
+            }
+          } else {
+            const uint32_t w[8] = {scaled(v[k]), scaled(v[r1]), scaled(v[r2]), scaled(v[r3]),
+                                   scaled(v[r4]), scaled(v[r5]), scaled(v[r6]), scaled(v[r7])};
+#pragma unroll
+            for (uint32_t i = 0; i < 8; ++i)
+              if (at + i < hz.limit) hz.z[at + i] = w[i];
+          }
+        }
+        return;
+      }
       constexpr int k1 = z_reg_at<T, ZM>(P, rp | 1u), k2 = z_reg_at<T, ZM>(P, rp | 2u),
                     k3 = z_reg_at<T, ZM>(P, rp | 3u);
       constexpr bool group = V4 && (rp & 3u) == 0u && k1 >= 0 && k2 >= 0 && k3 >= 0;
