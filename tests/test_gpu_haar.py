@@ -143,6 +143,29 @@ def test_forward_with_haar_side_output_in_place_and_tail(chw, m):
     assert np.all(buf[batch].cpu().numpy() == 7.0) and np.all(zbuf[batch].cpu().numpy() == 9.0)
 
 
+@pytest.mark.parametrize("m", [10, 14, 16])
+def test_forward_with_haar_side_output_16_byte_aligned_z(chw, m):
+    # z on a 16-byte but not 32-byte boundary: the captures that would leave as 32-byte
+    # stores go out as two 16-byte stores, same bits
+    import torch
+
+    batch = 5
+    x = _inputs(m, batch, "f32", 4200 + m)
+    p = chw.chw_plan(m, batch, "f32", "end")
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    zbuf = torch.full((batch * (1 << m) + 8,), 9.0, device="cuda")
+    assert zbuf.data_ptr() % 32 == 0
+    zd = zbuf[4: 4 + batch * (1 << m)].view(batch, 1 << m)  # 16 bytes past a 32-byte boundary
+    chw.chw_forward_haar(p, xd, yd, zd)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(p) == 0
+    assert_bitwise(zd.cpu().numpy(), O.haar_forward(x, m, np.float32, "end"), "side output")
+    assert_bitwise(yd.cpu().numpy(), O.chw_cascade(x, m, np.float32, "end"), "cascade")
+    rest = zbuf.cpu().numpy()
+    assert np.all(rest[:4] == 9.0) and np.all(rest[4 + batch * (1 << m):] == 9.0)
+
+
 def test_haar_argument_errors(chw):
     import torch
 
