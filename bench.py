@@ -321,6 +321,30 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
     st = torch.cuda.current_stream()
     g = torch.Generator(device=dev).manual_seed(7)
     k = max(3, steps // 2)
+    # the small configuration (m = 10, 64 signals, N(0,1) from seed 0, 256 KiB): a
+    # launch-latency workload, so its row states the time per call -- device time of
+    # back-to-back calls, and host wall time of one call plus a synchronize -- and its parity
+    x10 = W.normal_f32(10, 64, 0)
+    xd10 = torch.from_numpy(x10).to(dev)
+    yd10 = torch.empty_like(xd10)
+    p10 = chw.chw_plan(10, 64, "f32", "per_level")
+    ms = time_device(lambda: chw.chw_forward(p10, xd10, yd10), k, warmup, 1, st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        chw.chw_forward(p10, xd10, yd10)
+        torch.cuda.synchronize()
+    call_us = (time.perf_counter() - t0) / k * 1e6
+    got10 = yd10.cpu().numpy()
+    rec("m10_b64_f32_per_level", 2 * x10.nbytes, ms, 1,
+        oracle=(lambda: O.wht_dense(x10.astype(np.float64), 10), 2 * x10.nbytes, "64 signals, FP64 dense H_10 (O1)"),
+        device_us_per_call=round(ms * 1e3, 2), host_us_per_call_with_sync=round(call_us, 1),
+        bitwise_equal_to_fp32_cascade=bool(np.array_equal(
+            got10.view(np.uint32), O.chw_cascade(x10, 10, np.float32, "per_level").view(np.uint32))),
+        rel_err_vs_dense_fp64_max=float(O.rel_err_per_signal(got10, O.wht_dense(x10.astype(np.float64), 10)).max()),
+        rel_err_vs_fast_fp64_max=float(O.rel_err_per_signal(got10, O.wht_fast_dyadic(x10.astype(np.float64), 10)).max()),
+        error_gate=1e-6)
+    del xd10, yd10
     # fp32 per-level normalisation and int32 on the headline shape
     x = torch.randn(BATCH, 1 << M, device=dev, generator=g)
     y = torch.empty_like(x)

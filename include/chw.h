@@ -156,9 +156,13 @@ typedef struct chw_tune_choice_s {
  * passes); ordered plans cannot be combined with CHW_FLAG_ROWSTACK or ragged plans.
  * Tiers by m (chw_plan_get_info reports the one chosen): m <= 14 one CTA per tile in
  * registers and shared memory; m = 15, 16 one SM per signal with the signal held in tensor
- * memory; m = 17 (dyadic, natural) .. 29 two HBM passes; m = 17 in sequency order a
- * thread-block cluster.  CHW_FLAG_AUTOTUNE replaces these built-in choices by measured ones.
- * Allocates the plan (host) and its device workspace on the current device.  Returns
+ * memory; m = 17 in dyadic order two SMs per signal (a 2-CTA cluster, half of the signal
+ * in each SM's tensor memory, the last label bit exchanged through L2); m = 17 in natural
+ * order .. 30 two HBM passes; m = 17 in sequency order a thread-block cluster.
+ * CHW_FLAG_AUTOTUNE replaces these built-in choices by measured ones.
+ * Allocates the plan (host) and its device workspace on the current device: the two-pass
+ * intermediate (batch x 2^m elements), or for the m = 17 pair tier its exchange slots
+ * (128 KB per pair of SMs, 9.5 MB on 152 SMs).  Returns
  * CHW_ERR_INVALID_ARG / CHW_ERR_UNSUPPORTED / CHW_ERR_OOM / CHW_ERR_CUDA on failure, in
  * which case *plan is set to NULL.
  */

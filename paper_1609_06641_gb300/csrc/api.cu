@@ -449,13 +449,8 @@ chw_status_t launch_tmem_col_pass(chw_plan_s* p, int A, int clo, int var, const 
   return CHW_OK;
 }
 
-// Exchange scratch of the tensor-memory tier over SM pairs (m = 17): four 32 KB slots per
-// cluster, one cluster per two SMs of the device.
-size_t cross_scratch_bytes(int device) {
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  return static_cast<size_t>(sms >= 2 ? sms / 2 : 1) << 17;
-}
+// Exchange scratch of the tensor-memory tier over SM pairs (m = 17).
+size_t cross_scratch_bytes(int device) { return static_cast<size_t>(chw::tmem_cross_clusters(device)) << 17; }
 
 // Tensor-memory tier over a cluster (m = 17: two SMs per signal, each holding half of it);
 // `ws` holds at least cross_scratch_bytes().

@@ -126,5 +126,13 @@ TmemLaunchFn lookup_tmem_col(int m, int clo, int var);
 // other m.
 TmemLaunchFn lookup_tmem_cross(int m, int var);
 
+// Clusters the m = 17 pair kernel's exchange scratch must hold on `device` (one per two
+// SMs, the most that can be resident); each takes four 32 KB slots (128 KB).
+inline int64_t tmem_cross_clusters(int device) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return sms >= 2 ? sms / 2 : 1;
+}
+
 }  // namespace chw
 

@@ -124,14 +124,6 @@ bool tmem_opt(int m, int opt) { return m >= 15 && m <= 17 && opt == 2; }
 
 bool two_pass_opt(int m, int opt) { return m >= 18 || (m == 17 && opt == 1); }
 
-// Exchange slots of the m = 17 pair kernel: four 32 KB slots per cluster, one cluster per
-// two SMs.
-int64_t cross_clusters() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms >= 2 ? sms / 2 : 1;
-}
 
 // The output of a tensor-memory launch over the whole packed array: rows of 2^(m-8) words,
 // boxes of 32 words x 256 rows (one signal), SWIZZLE_128B.  Rows past the last whole one
@@ -364,7 +356,9 @@ RaggedPlan* ragged_create_at(const uint8_t* ms, const int64_t* offsets, int64_t 
                 (total >> (m - 8)) >= 256;
     g.opt = default_option(m, g.aligned);
     if (m == 17 && g.aligned && r->d_xscratch == nullptr && e == cudaSuccess) {
-      r->xclusters = cross_clusters();
+      int dev = 0;
+      cudaGetDevice(&dev);
+      r->xclusters = tmem_cross_clusters(dev);
       e = cudaMalloc(&r->d_xscratch, static_cast<size_t>(r->xclusters) << 17);
     }
     e = cudaMalloc(&g.d_off, go.size() * sizeof(int64_t));
