@@ -335,10 +335,27 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
         chw.chw_forward(p10, xd10, yd10)
         torch.cuda.synchronize()
     call_us = (time.perf_counter() - t0) / k * 1e6
+    # the device's own latency: the call captured once in a CUDA graph and replayed (no host
+    # work between launches)
+    graph_us = None
+    try:
+        cs = torch.cuda.Stream()
+        cs.wait_stream(st)
+        with torch.cuda.stream(cs):
+            chw.chw_forward(p10, xd10, yd10)
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=cs):
+                chw.chw_forward(p10, xd10, yd10)
+        st.wait_stream(cs)
+        torch.cuda.synchronize()
+        graph_us = round(time_device(gr.replay, k, warmup, 1, st) * 1e3, 2)
+    except RuntimeError:
+        graph_us = None
     got10 = yd10.cpu().numpy()
     rec("m10_b64_f32_per_level", 2 * x10.nbytes, ms, 1,
         oracle=(lambda: O.wht_dense(x10.astype(np.float64), 10), 2 * x10.nbytes, "64 signals, FP64 dense H_10 (O1)"),
         device_us_per_call=round(ms * 1e3, 2), host_us_per_call_with_sync=round(call_us, 1),
+        graph_replay_us_per_call=graph_us,
         bitwise_equal_to_fp32_cascade=bool(np.array_equal(
             got10.view(np.uint32), O.chw_cascade(x10, 10, np.float32, "per_level").view(np.uint32))),
         rel_err_vs_dense_fp64_max=float(O.rel_err_per_signal(got10, O.wht_dense(x10.astype(np.float64), 10)).max()),
