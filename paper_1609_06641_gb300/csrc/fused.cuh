@@ -553,21 +553,7 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
       check_fail(args.status, addr);
       continue;
     }
-    if (args.diag_out != nullptr) {
-      const int8_t* d = args.diag_out;
-      const int64_t di = addr & args.diag_mask;  // D acts on the stored (final) positions
-      if constexpr (std::is_same_v<BF, BfI32>) {
-        if (d[di] < 0) q.x = 0u - q.x;
-        if (d[di + 1] < 0) q.y = 0u - q.y;
-        if (d[di + 2] < 0) q.z = 0u - q.z;
-        if (d[di + 3] < 0) q.w = 0u - q.w;
-      } else {
-        if (d[di] < 0) q.x ^= 0x80000000u;
-        if (d[di + 1] < 0) q.y ^= 0x80000000u;
-        if (d[di + 2] < 0) q.z ^= 0x80000000u;
-        if (d[di + 3] < 0) q.w ^= 0x80000000u;
-      }
-    }
+    if (args.diag_out != nullptr) diag4_at<BF>(q, args, addr);  // D acts on the stored (final) positions
     st_global_v4(out + addr, q.x, q.y, q.z, q.w);
   }
   };
@@ -575,6 +561,81 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
     loop(std::true_type{});
   } else {
     loop(std::false_type{});
+  }
+}
+
+// ------------------------------------------------------------------ the diagonal D
+// D is an int8 array of +-1: a value's sign flips where its byte is negative (int32:
+// negated), i.e. where the byte's top bit is set.
+template <class BF>
+__device__ __forceinline__ uint32_t diag_apply(uint32_t v, uint32_t top) {  // top: 0 or bit 31
+  if constexpr (std::is_same_v<BF, BfI32>) {
+    const uint32_t s = static_cast<uint32_t>(static_cast<int32_t>(top) >> 31);
+    return (v ^ s) - s;
+  } else {
+    return v ^ top;
+  }
+}
+// The top bit of byte j (0..3) of w, moved to bit 31.
+__device__ __forceinline__ uint32_t byte_top(uint32_t w, int j) { return (w << (24 - 8 * j)) & 0x80000000u; }
+// D read as 16-byte vectors: base pointer 16-byte aligned and positions taken modulo at
+// least 16 (so a run of 16 never wraps).
+__device__ __forceinline__ bool diag_v16_ok(const int8_t* d, int64_t mask) {
+  return (reinterpret_cast<uintptr_t>(d) & 15u) == 0u && (mask & 15) == 15;
+}
+// D on a run of 16 values at consecutive positions, from one 16-byte load (d 16-aligned).
+template <class BF, int N, class IDX>
+__device__ __forceinline__ void diag16(uint32_t (&v)[N], const int8_t* d, IDX idx) {
+  const uint4 w = *reinterpret_cast<const uint4*>(d);
+  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+  sfor<16>([&](auto jj) {
+    constexpr int j = jj;
+    v[idx(j)] = diag_apply<BF>(v[idx(j)], byte_top(ws[j >> 2], j & 3));
+  });
+}
+
+// D on four consecutive output positions from `pos` (a multiple of 4): one 4-byte load of
+// D where the array allows it.
+template <class BF>
+__device__ __forceinline__ void diag4_at(uint4& q, const FusedArgs& args, int64_t pos) {
+  const int8_t* d = args.diag_out;
+  const int64_t di = pos & args.diag_mask;
+  if ((reinterpret_cast<uintptr_t>(d) & 3u) == 0u && (args.diag_mask & 3) == 3) {
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(d + di);
+    q.x = diag_apply<BF>(q.x, byte_top(w, 0));
+    q.y = diag_apply<BF>(q.y, byte_top(w, 1));
+    q.z = diag_apply<BF>(q.z, byte_top(w, 2));
+    q.w = diag_apply<BF>(q.w, byte_top(w, 3));
+  } else {
+    q.x = diag_apply<BF>(q.x, d[di] < 0 ? 0x80000000u : 0u);
+    q.y = diag_apply<BF>(q.y, d[(di + 1) & args.diag_mask] < 0 ? 0x80000000u : 0u);
+    q.z = diag_apply<BF>(q.z, d[(di + 2) & args.diag_mask] < 0 ? 0x80000000u : 0u);
+    q.w = diag_apply<BF>(q.w, d[(di + 3) & args.diag_mask] < 0 ? 0x80000000u : 0u);
+  }
+}
+
+// D on the inputs of phase 1 (the adjoint's D): register k holds label tl | reg_label(k),
+// and registers 16 g .. 16 g + 15 hold 16 consecutive positions (phase 1 keeps label bits
+// 0..3 on register bits 0..3), so each group takes one 16-byte load of D.
+template <Phase P, class BF>
+__device__ __forceinline__ void diag_in_phase1(uint32_t (&v)[64], const FusedArgs& args, int64_t in_elem0,
+                                               uint32_t tl) {
+  static_assert((reg_label(P, 1) | reg_label(P, 2) | reg_label(P, 4) | reg_label(P, 8)) == 15u &&
+                    reg_label(P, 1) == 1u && reg_label(P, 2) == 2u && reg_label(P, 4) == 4u && reg_label(P, 8) == 8u,
+                "phase 1 holds label bits 0..3 on register bits 0..3");
+  const int8_t* d = args.diag_in;
+  if (diag_v16_ok(d, args.diag_mask) && ((in_elem0 + tl) & 15) == 0) {
+    sfor<4>([&](auto gg) {
+      constexpr int g = gg;
+      const int64_t at = (in_elem0 + (tl | reg_label(P, 16 * g))) & args.diag_mask;
+      diag16<BF>(v, d + at, [](int j) { return 16 * g + j; });
+    });
+  } else {
+    sfor<64>([&](auto k) {
+      constexpr uint32_t kl = reg_label(P, k);
+      const int64_t idx = in_elem0 + (tl | kl);
+      if (d[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
+    });
   }
 }
 
@@ -755,14 +816,7 @@ __device__ __forceinline__ void phases_1_2(uint32_t (&v)[64], int64_t in_elem0, 
   if constexpr (F.has_p1) {
     const uint32_t base = thread_pos<P1, LS, LMASK>(lane, warp, 0);
     load_phase<P1, LS, LMASK>(v, buf, base);
-    if (args.diag_in != nullptr) {
-      const uint32_t tl = thread_label<P1>(lane, warp, 0);
-      sfor<64>([&](auto k) {
-        constexpr uint32_t kl = reg_label(P1, k);
-        const int64_t idx = in_elem0 + (tl | kl);
-        if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
-      });
-    }
+    if (args.diag_in != nullptr) diag_in_phase1<P1, BF>(v, args, in_elem0, thread_label<P1>(lane, warp, 0));
     bfly<P1, 0, 5, HM, BF, ZM, ZEND>(v, bf, lane, warp, hz);
     store_phase<P1, P1, LS, LMASK>(v, buf, base);
     __syncthreads();
@@ -870,14 +924,7 @@ __device__ __forceinline__ void tile_compute(int64_t in_elem0, int64_t out_base,
   } else if constexpr (F.has_p1) {
     const uint32_t base = thread_pos<P1, LS, LMASK>(lane, warp, 0);
     load_phase<P1, LS, LMASK>(v, buf, base);
-    if (args.diag_in != nullptr) {
-      const uint32_t tl = thread_label<P1>(lane, warp, 0);
-      sfor<64>([&](auto k) {
-        constexpr uint32_t kl = reg_label(P1, k);
-        const int64_t idx = in_elem0 + (tl | kl);
-        if (args.diag_in[idx & args.diag_mask] < 0) v[k] = std::is_same_v<BF, BfI32> ? 0u - v[k] : v[k] ^ 0x80000000u;
-      });
-    }
+    if (args.diag_in != nullptr) diag_in_phase1<P1, BF>(v, args, in_elem0, thread_label<P1>(lane, warp, 0));
     bfly<P1, 0, (TLO + M < 5 ? TLO + M : 5), HM, BF, ZM, ZEND>(v, bf, lane, warp, &hz);
     if constexpr (F.p1_final) {
       scale_all();

@@ -479,12 +479,19 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
     }
     const int64_t ob = unit_elem<M + XP>(args, args.out_off, first + k * stride);
     const uint32_t xr = 64u * ((static_cast<uint32_t>(q) << 1) | rank);  // within the output run
-    if (args.diag_out != nullptr) {  // D acts on the stored positions
+    if (args.diag_out != nullptr) {  // D acts on the stored positions (64 consecutive)
       const int64_t at = (static_cast<int64_t>(rho) << (M + XP - 8)) + xr;
       const int8_t* d = args.diag_out + (at & args.diag_mask);
+      if (diag_v16_ok(args.diag_out, args.diag_mask)) {
+        sfor<4>([&](auto gg) {
+          constexpr int g = gg;
+          diag16<BF>(v, d + 16 * g, [](int j) { return 16 * g + j; });
+        });
+      } else {
 #pragma unroll
-      for (int i = 0; i < 64; ++i)
-        if (d[i] < 0) v[i] = std::is_same_v<BF, BfI32> ? 0u - v[i] : v[i] ^ 0x80000000u;
+        for (int i = 0; i < 64; ++i)
+          if (d[i] < 0) v[i] = std::is_same_v<BF, BfI32> ? 0u - v[i] : v[i] ^ 0x80000000u;
+      }
     }
     if (tid == 0) bulk_wait_read();  // the previous chunk's TMA stores have read the buffer
     __syncthreads();                 // ... and every thread has read its values from xbuf
@@ -663,14 +670,22 @@ __global__ void __launch_bounds__(kTmemThreads, 1)
       }
     } else {
       if (OM == 0 && args.diag_out != nullptr) {  // D acts on the stored positions
-        // (a column tile's outputs are a part of a longer signal: its place in it counts)
+        // (a column tile's outputs are a part of a longer signal: its place in it counts);
+        // the thread's 64 outputs of the chunk are consecutive: four 16-byte loads of D
         const int64_t at = (CLO > 0 ? ob : 0) + (static_cast<int64_t>(rho) << (M - 8));
-        const int8_t* d = args.diag_out + (at & args.diag_mask);
-        sfor<64>([&](auto ww) {
-          constexpr int w = ww;
-          constexpr int si = T::src(0, w);
-          if (d[64 * q + w] < 0) u[si] = std::is_same_v<BF, BfI32> ? 0u - u[si] : u[si] ^ 0x80000000u;
-        });
+        const int8_t* d = args.diag_out + (at & args.diag_mask) + 64 * q;
+        if (diag_v16_ok(args.diag_out, args.diag_mask)) {
+          sfor<4>([&](auto gg) {
+            constexpr int g = gg;
+            diag16<BF>(u, d + 16 * g, [](int j) { return T::src(0, 16 * g + j); });
+          });
+        } else {
+          sfor<64>([&](auto ww) {
+            constexpr int w = ww;
+            constexpr int si = T::src(0, w);
+            if (d[w] < 0) u[si] = std::is_same_v<BF, BfI32> ? 0u - u[si] : u[si] ^ 0x80000000u;
+          });
+        }
       }
       if (tid == 0) bulk_wait_read();  // the previous chunk's TMA stores have read the buffer
       __syncthreads();

@@ -197,6 +197,33 @@ def test_diag_forward_and_adjoint(chw, torch, m):
     assert_bitwise(got_a, ref_a, f"H^T D y m={m}")
 
 
+@pytest.mark.parametrize("m", [0, 1, 6, 14, 16, 17, 19])
+@pytest.mark.parametrize("shift", [0, 1, 4])
+def test_diag_at_any_byte_offset(chw, torch, m, shift):
+    # D may start at any byte: an array on a 16-byte (4-byte) boundary is read 16 (4) bytes
+    # at a time, others byte by byte -- the same signs either way, forward (D on the
+    # outputs, also through the tiles' TMA store) and adjoint (D on the inputs)
+    n = 1 << m
+    batch = 3 if m >= 13 else max(3, (1 << (14 - m)) + 3)
+    x = W.normal_f32(m, batch, seed=900 + m)
+    d = W.diag_pm1(m, seed=7 + m)
+    dev = torch.device("cuda:0")
+    dbuf = torch.zeros(n + 32, dtype=torch.int8, device=dev)
+    assert dbuf.data_ptr() % 16 == 0
+    dd = dbuf[shift: shift + n]
+    dd.copy_(torch.from_numpy(d))
+    p = chw.chw_plan(m, batch, "f32", "end")
+    xd = torch.from_numpy(x).to(dev)
+    yf, ya = torch.empty_like(xd), torch.empty_like(xd)
+    chw.chw_forward(p, xd, yf, diag=dd)
+    chw.chw_adjoint(p, xd, ya, diag=dd)
+    torch.cuda.synchronize()
+    assert chw.chw_last_device_status(p) == 0
+    assert_bitwise(yf.cpu().numpy(), O.chw_cascade(x, m, np.float32, "end") * d.astype(np.float32), f"D H x m={m}")
+    ref_a = O.chw_reverse_cascade(x * d.astype(np.float32), m, np.float32, "end")
+    assert_bitwise(ya.cpu().numpy(), ref_a, f"H^T D y m={m}")
+
+
 def test_round_trip_identity(chw, torch):
     m = 16
     x = W.normal_f32(m, 8, seed=1)
