@@ -1,6 +1,5 @@
 // Launchers of the tensor-memory kernel for signals spread over a cluster of SMs (tmem.cuh
-// with XP > 0): m = 17 on two SMs and m = 18 on four, dyadic order, every butterfly
-// variant.
+// with XP = 1): m = 17 on two SMs, dyadic order, every butterfly variant.
 #include "tmem_launch.cuh"
 
 namespace chw {
