@@ -296,8 +296,24 @@ __device__ __forceinline__ void butterflies_head(uint32_t (&v)[64], const BF& bf
       const bool live = (tl & above) != 0u;
       sfor<64>([&](auto kk) {
         constexpr int k = kk;
-        if constexpr (((k >> i) & 1) == 0) {
-          if constexpr ((reg_label(P, k) & above) != 0u) {
+        constexpr bool s0 = (reg_label(P, k) & above) != 0u;
+        if constexpr (BF::kPacked && i >= 1) {
+          // registers k and k | 1 travel together (one f32x2 pair) where both are live or
+          // both depend on the thread's label the same way
+          constexpr bool s1 = (reg_label(P, k | 1) & above) != 0u;
+          if constexpr (((k >> i) & 1) == 0 && (k & 1) == 0) {
+            constexpr int j = 1 << i;
+            if constexpr (s0 && s1) {
+              bf.pair(v[k], v[k | 1], v[k | j], v[k | 1 | j]);
+            } else if constexpr (!s0 && !s1) {
+              if (live) bf.pair(v[k], v[k | 1], v[k | j], v[k | 1 | j]);
+            } else {
+              if (s0 || live) bf(v[k], v[k | j]);
+              if (s1 || live) bf(v[k | 1], v[k | 1 | j]);
+            }
+          }
+        } else if constexpr (((k >> i) & 1) == 0) {
+          if constexpr (s0) {
             bf(v[k], v[k | (1 << i)]);
           } else {
             if (live) bf(v[k], v[k | (1 << i)]);

@@ -486,6 +486,42 @@ __device__ __forceinline__ void copy_out(const uint32_t* buf, int64_t out_base, 
   constexpr int NCH = 1 << (TB - 2);
   constexpr int S = F.stage_s;
   constexpr bool ROWS = tile_store_layout(OUTMODE, CB);
+  if constexpr (OUTMODE == 6) {
+    // Haar-Walsh head: the staged tile holds every signal of 2^M words in dyadic order of
+    // its labels, and final position p >= 1 (scale k = the top bit of p) takes staged
+    // element ((p - 2^k) << (M - k)) | 2^(M-1-k), p = 0 element 0.  Each thread gathers the
+    // four staged elements of four consecutive final positions and stores them as 16 bytes.
+    constexpr uint32_t mask = (1u << M) - 1u;
+    for (int c = threadIdx.x; c < NCH; c += NT) {
+      const uint32_t o = static_cast<uint32_t>(c) << 2;  // final position within the tile
+      const int64_t at = out_base + o;
+      if (at >= args.out_total) continue;
+      uint32_t e[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const uint32_t pf = (o + t) & mask, so = (o + t) & ~mask;
+        uint32_t qe = 0;
+        int k = 0;
+        if (pf != 0) {
+          k = 31 - __clz(pf);
+          qe = ((pf - (1u << k)) << (M - k)) | (1u << (M - 1 - k));
+        }
+        e[t] = buf[staged_pos(so + qe, S, ROWS)];
+        if (args.head_end && pf != 0) e[t] = __float_as_uint(__fmul_rn(__uint_as_float(e[t]), end_scale_dev(k)));
+      }
+      const int64_t nv = args.out_total - at < 4 ? args.out_total - at : 4;  // a tail chunk holds fewer
+      if (args.checked && !range_ok(at, nv, args.out_total)) {
+        check_fail(args.status, at);
+      } else if (at + 3 < args.out_total) {
+        st_global_v4(out + at, e[0], e[1], e[2], e[3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (at + t < args.out_total) out[at + t] = e[t];
+      }
+    }
+    return;
+  }
   // the same loop with and without the checked mode's range checks, chosen once
   auto loop = [&](auto checked_c) {
   constexpr bool CHECKED = decltype(checked_c)::value;
