@@ -115,7 +115,43 @@ void tmem_natural() {
   std::printf("tmem natural M=%d ok\n", M);
 }
 
+// Haar-Walsh head (output mode 6): the copy-out gathers final position p of a signal of
+// 2^M words from staged (dyadic-order) element qe = ((p - 2^k) << (M - k)) | 2^(M-1-k),
+// k = the top bit of p (p = 0: qe = 0), restated from the kernel.  By eq. (4) scale k
+// holds H_k of the signal's block [2^k, 2^(k+1)) in dyadic order, so final position
+// 2^k + bitrev_k(j) is the block's label 2^k + j, staged at dyadic position
+// bitrev_M(2^k + j).  Every final position must take that element, each exactly once.
+static uint32_t bitrev(uint32_t x, int n) {
+  uint32_t r = 0;
+  for (int i = 0; i < n; ++i) r |= ((x >> i) & 1u) << (n - 1 - i);
+  return r;
+}
+void head_gather(int M) {
+  const uint32_t n = 1u << M;
+  std::vector<int> used(n, 0);
+  for (uint32_t p = 0; p < n; ++p) {
+    uint32_t qe = 0;
+    if (p != 0) {
+      int k = 31;
+      while (((p >> k) & 1u) == 0) --k;
+      qe = ((p - (1u << k)) << (M - k)) | (1u << (M - 1 - k));
+    }
+    // the definition: the label whose final position is p
+    uint32_t label = 0;
+    if (p != 0) {
+      int k = 31;
+      while (((p >> k) & 1u) == 0) --k;
+      label = (1u << k) + bitrev(p - (1u << k), k);
+    }
+    CHECK(qe < n && qe == bitrev(label, M), "head M=%d: final %u gathers %u, expected %u", M, p, qe, bitrev(label, M));
+    used[qe]++;
+  }
+  for (uint32_t i = 0; i < n; ++i) CHECK(used[i] == 1, "head M=%d: staged %u used %d times", M, i, used[i]);
+  std::printf("head M=%d ok\n", M);
+}
+
 int main() {
+  for (int M = 0; M <= 14; ++M) head_gather(M);
   fused_tile_store<0, 0, 13>();
   fused_tile_store<0, 3, 13>();
   fused_tile_store<0, 7, 13>();
