@@ -1191,10 +1191,11 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
     p->workspace_bytes = static_cast<size_t>(p->rowstack_slots << m) * elem_bytes(dtype);
     e = cudaMalloc(&p->workspace, p->workspace_bytes);
     if (e != cudaSuccess) {
+      const size_t bytes = p->workspace_bytes;
       cudaFree(p->d_status);
       delete p;
       cudaGetLastError();
-      return fail(CHW_ERR_OOM, "workspace of %zu bytes: %s", p->workspace_bytes, cudaGetErrorString(e));
+      return fail(CHW_ERR_OOM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
     }
   }
   if (p->tier == kTierTwoPass || p->tier == kTierTmemCross) {
@@ -1202,10 +1203,11 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
                                                    : static_cast<size_t>(p->total) * elem_bytes(dtype);
     e = cudaMalloc(&p->workspace, p->workspace_bytes);
     if (e != cudaSuccess) {
+      const size_t bytes = p->workspace_bytes;
       cudaFree(p->d_status);
       delete p;
       cudaGetLastError();
-      return fail(CHW_ERR_OOM, "workspace of %zu bytes: %s", p->workspace_bytes, cudaGetErrorString(e));
+      return fail(CHW_ERR_OOM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
     }
   }
   if (!is_lowp(dtype)) {

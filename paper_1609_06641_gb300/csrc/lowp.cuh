@@ -277,12 +277,12 @@ constexpr bool xpos_bijective() {
 constexpr bool exchange_conflict_free() {
   for (int i = 0; i < 128; i += 4) {
     // phase 1 writes: lanes 8q..8q+7 carry label bits 6..8 (lane bits 0..2)
-    for (int q = 0; q < 4; ++q) {
+    for (uint32_t q = 0; q < 4; ++q) {
       int seen = 0;
       for (uint32_t l = 8 * q; l < 8 * q + 8; ++l) seen |= 1 << ((xpos(p1_label(i) | (l << 6)) >> 2) & 7u);
       if (seen != 0xff) return false;
     }
-    for (int q = 0; q < 4; ++q) {
+    for (uint32_t q = 0; q < 4; ++q) {
       int seen = 0;
       for (uint32_t l = 8 * q; l < 8 * q + 8; ++l) seen |= 1 << ((xpos(p2_label(i) | p2_lane_label(l)) >> 2) & 7u);
       if (seen != 0xff) return false;
