@@ -82,3 +82,35 @@ def test_noalloc_rejects_what_it_cannot_hold(env):
     assert lib.chw_forward_noalloc(18, 1, _lib.CHW_BF16, _lib.CHW_NORM_END, p, p, None) == _lib.CHW_ERR_UNSUPPORTED
     assert lib.chw_forward_noalloc(18, 1, _lib.CHW_F32, _lib.CHW_NORM_END, ctypes.c_void_p(xd.data_ptr() + 4), p, None) == _lib.CHW_ERR_ALIGNMENT
     assert lib.chw_noalloc_device_status() == _lib.CHW_OK
+
+
+def test_noalloc_call_replays_from_a_cuda_graph(env):
+    """A call captured into a CUDA graph (after one warm-up call outside the capture, which
+    does the per-kernel set-up) replays to chw_forward's bits and the fp32 cascade's, with
+    the status word at CHW_OK: the call allocates nothing, so it may be captured."""
+    chw, _lib, lib, torch = env
+    m, batch = 20, 2
+    d, nm = chw.DTYPES["f32"], chw.NORMS["end"]
+    x = W.normal_f32(m, batch, seed=61)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    noalloc(lib, torch, m, batch, d, nm, xd)  # warm-up
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        st = lib.chw_forward_noalloc(m, batch, d, nm, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()),
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == _lib.CHW_OK, lib.chw_status_string(st).decode()
+    for _ in range(2):
+        yd.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert lib.chw_noalloc_device_status() == _lib.CHW_OK, lib.chw_last_error_message().decode()
+        p = chw.chw_plan(m, batch, "f32", "end")
+        ref = torch.empty_like(xd)
+        chw.chw_forward(p, xd, ref)
+        torch.cuda.synchronize()
+        g, r = yd.cpu().numpy(), ref.cpu().numpy()
+        assert np.array_equal(g.view(np.uint32), r.view(np.uint32)), "graph replay differs from chw_forward"
+        want = oracle.chw_cascade(x, m, np.float32, "end")
+        assert np.array_equal(g.view(np.uint32), want.view(np.uint32)), "graph replay differs from the cascade"
