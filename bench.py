@@ -491,7 +491,16 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
         bytes_counted="x read once, y and z written once (3 n 4 bytes per signal)",
         oracle=(lambda: (O.chw_cascade(h16, M, np.float32, "per_level"), O.haar_forward(h16, M, np.float32, "per_level")),
                 3 * h16.nbytes, "2 signals, fp32 cascade and fp32 Haar"))
-    del xh, zh, yh, ph
+    # the same two calls with normalisation at the end (one scale per output instead of one
+    # per level): the plans `--op haar_walsh` and `--op forward_haar` time
+    pe = chw.chw_plan(M, BATCH, "f32", "end", chw.CHW_FLAG_HAAR_WALSH)
+    ms = time_device(lambda: chw.chw_from_haar(pe, zh, yh), k, warmup, 1, st)
+    rec("m16_b4096_f32_haar_walsh_end", 2 * nb, ms, 3)
+    pf = chw.chw_plan(M, BATCH, "f32", "end")
+    ms = time_device(lambda: chw.chw_forward_haar(pf, xh, yh, zh), k, warmup, 1, st)
+    rec("m16_b4096_f32_forward_with_haar_output_end", 3 * nb, ms, 1,
+        bytes_counted="x read once, y and z written once (3 n 4 bytes per signal)")
+    del xh, zh, yh, ph, pe, pf
     # natural and sequency output orders on the headline shape and at m = 12
     for order in ("natural", "sequency"):
         for m, b in ((M, BATCH), (12, 65536)):
@@ -770,7 +779,10 @@ def main():
         line["cpu_baseline"] = cpu
         line["error"] = {"max_rel_err_vs_fp64_oracle": err, "signals_checked": len(rows), "gate": 1e-6}
         if not args.no_extra:
-            line["extra"] = extra_measurements(chw, torch, dev, args.steps, args.warmup, peak)
+            try:
+                line["extra"] = extra_measurements(chw, torch, dev, args.steps, args.warmup, peak)
+            except Exception as e:  # the headline line is printed whatever happens to the extras
+                line["extra"] = {"failed": repr(e)[:400]}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
