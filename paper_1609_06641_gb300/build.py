@@ -156,7 +156,7 @@ def _sources():
 
 def _digest():
     h = hashlib.sha256()
-    files = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh")))
+    files = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h")))
     files.append(os.path.join(ROOT, "include", "chw.h"))
     files.append(os.path.abspath(__file__))
     for f in files:

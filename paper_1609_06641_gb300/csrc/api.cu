@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/chw.h"
+#include "colblock.h"
 #include "launch.cuh"
 #include "ragged.cuh"
 #include "simple.cuh"
@@ -193,29 +194,17 @@ chw_status_t make_seq_map(CUtensorMap* map, const void* ptr, int64_t total, int 
   return CHW_OK;
 }
 
-// The column-blocked scratch of a two-pass split (rows of 2^M words, 2^a rows per signal,
-// blocks of 2^c columns, c = 2..5) as the 5-D view {2^c words, row r, block g mod
-// 2^(M-8-c), run g >> (M-8-c), signal}: element k of row r of signal s at s 2^(a+M) +
-// (k >> c) 2^(a+c) + 2^c r + (k mod 2^c); boxes of 2^c words x 1 x 2^(5-c) blocks x 256
-// runs x 1.  The box's rows of 2^c words are dense in shared memory only when the swizzle
-// span equals their width (a narrower row takes a whole span), so the swizzle is 128, 64
-// or 32 bytes for c = 5, 4, 3 and none for c = 2: a box is 32 KB, 256 runs of 128 bytes,
-// with the 16-byte pieces of run rho XOR-permuted by rho mod 8, 4, 2 or 1 -- the layout in
-// which the tensor-memory kernel stages such a first pass.  False if the driver rejects
-// the view.
+// The column-blocked scratch of a two-pass split as the 5-D view `colblock_view` gives: boxes
+// of 256 runs of 128 bytes, with the 16-byte pieces of run rho XOR-permuted by rho mod 8,
+// 4, 2 or 1 for 32-, 16-, 8- or 4-column blocks -- the layout in which the tensor-memory
+// kernel stages such a first pass.  False if the driver rejects the view.
 bool make_colblock_map(CUtensorMap* map, const void* ptr, int64_t total, int M, int a, int c) {
   auto enc = tensor_map_encoder();
   if (!enc || M < 13 || c < 2 || c > 5 || total % (int64_t{1} << (a + M)) != 0) return false;
-  const cuuint64_t w = 4;
-  cuuint64_t dims[5] = {cuuint64_t{1} << c, cuuint64_t{1} << a, cuuint64_t{1} << (M - 8 - c), 256,
-                        static_cast<cuuint64_t>(total >> (a + M))};
-  cuuint64_t strides[4] = {w << c, w << (a + c), w << (a + M - 8), w << (a + M)};
-  cuuint32_t box[5] = {1u << c, 1, 1u << (5 - c), 256, 1};
-  const CUtensorMapSwizzle sw[4] = {CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_SWIZZLE_64B,
-                                    CU_TENSOR_MAP_SWIZZLE_128B};
+  const chw::ColblockView v = chw::colblock_view(total, M, a, c);
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, const_cast<void*>(ptr), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, sw[c - 2], CU_TENSOR_MAP_L2_PROMOTION_NONE,
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, const_cast<void*>(ptr), v.dims, v.strides, v.box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, v.swizzle, CU_TENSOR_MAP_L2_PROMOTION_NONE,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -1,9 +1,12 @@
 // Host-only check of the staging layouts the kernels' TMA stores rely on, computed with the
-// kernels' own constexpr plans (no GPU): every staged position is hit exactly once and the
-// TMA box that reads it writes the output position the cascade defines.  Prints "ALL OK".
+// kernels' own constexpr plans and, for the column-blocked first pass of a two-pass split,
+// the plan's own tensor view (no GPU): every staged position is hit exactly once, the TMA
+// box that reads it fits the buffer it is read from and writes the output position the
+// cascade defines.  Prints "ALL OK".
 #include <cstdio>
 #include <vector>
 
+#include "colblock.h"
 #include "tmem.cuh"
 
 using namespace chw;
@@ -46,6 +49,34 @@ uint32_t thread_label_host(const Phase& p, uint32_t lane, uint32_t warp) {
   return lane_label(p, static_cast<int>(lane)) | warp_label(p, static_cast<int>(warp));
 }
 
+// Tensor-memory kernel, dyadic order (output modes 0 and 1): the labels staged for output
+// chunk q.  Run rho's 16-byte piece c (0..15: half c / 8 of its 64 outputs) lands at piece
+// (c mod 8) ^ (rho & skey) of row rho of half c / 8 of the staging buffer; -1 where nothing
+// is staged; *ok turns false if two values share a word.
+template <int M>
+std::vector<int64_t> stage_dyadic(int q, uint32_t skey, bool* ok) {
+  using T = TmemCfg<M, 0>;
+  std::vector<int64_t> stage(1u << kTmemTB, -1);
+  for (uint32_t warp = 0; warp < 8; ++warp)
+    for (uint32_t lane = 0; lane < 32; ++lane) {
+      const uint32_t tl = thread_label_host(T::P3, lane, warp);
+      const uint32_t rho = bitrev_bits(tl, 8), sxor = (rho & skey) << 2;
+      for (int c = 0; c < 16; ++c)
+        for (int e = 0; e < 4; ++e) {
+          const int si = T::src(q, 4 * c + e);
+          const int r = si / T::JW, j = si % T::JW;
+          const uint32_t label = tl | reg_label(T::P3, q * T::JW + j) | (static_cast<uint32_t>(r) << kTmemTB);
+          const uint32_t p = ((c >> 3) << (kTmemTB - 1)) + (((rho << 5) | (4u * (c & 7))) ^ sxor) + e;
+          if (stage[p] >= 0) {
+            std::printf("tmem M=%d q=%d: staged twice at %u\n", M, q, p);
+            *ok = false;
+          }
+          stage[p] = label;
+        }
+    }
+  return stage;
+}
+
 // Tensor-memory kernel, dyadic order: chunk q's staging (two 32-word x 256-row boxes,
 // SWIZZLE_128B) against the dyadic output position bitrev_M(label).
 template <int M>
@@ -54,21 +85,9 @@ void tmem_dyadic() {
   const uint32_t n = 1u << M;
   std::vector<int> out(n, 0);
   for (int q = 0; q < T::R; ++q) {
-    std::vector<int64_t> stage(1u << kTmemTB, -1);
-    for (uint32_t warp = 0; warp < 8; ++warp)
-      for (uint32_t lane = 0; lane < 32; ++lane) {
-        const uint32_t tl = thread_label_host(T::P3, lane, warp);
-        const uint32_t rho = bitrev_bits(tl, 8), sxor = (rho & 7u) << 2;
-        for (int c = 0; c < 16; ++c)
-          for (int e = 0; e < 4; ++e) {
-            const int si = T::src(q, 4 * c + e);
-            const int r = si / T::JW, j = si % T::JW;
-            const uint32_t label = tl | reg_label(T::P3, q * T::JW + j) | (static_cast<uint32_t>(r) << kTmemTB);
-            const uint32_t p = ((c >> 3) << (kTmemTB - 1)) + (((rho << 5) | (4u * (c & 7))) ^ sxor) + e;
-            CHECK(stage[p] < 0, "tmem M=%d q=%d: staged twice at %u", M, q, p);
-            stage[p] = label;
-          }
-      }
+    bool ok = true;
+    const std::vector<int64_t> stage = stage_dyadic<M>(q, 7u, &ok);
+    CHECK(ok, "tmem M=%d: staging", M);
     for (uint32_t h = 0; h < 2; ++h)
       for (uint32_t row = 0; row < 256; ++row)
         for (uint32_t x = 0; x < 32; ++x) {
@@ -80,6 +99,65 @@ void tmem_dyadic() {
   }
   for (uint32_t i = 0; i < n; ++i) CHECK(out[i] == 1, "tmem M=%d: output %u written %d times", M, i, out[i]);
   std::printf("tmem dyadic M=%d ok\n", M);
+}
+
+// Tensor-memory kernel as the first pass of a two-pass split (output mode 1), its chunks
+// written by TMA stores through the column-blocked view `colblock_view` (the plan's own
+// encoding).  The kernel stages with key 2^(c-2) - 1 for blocks of 2^c columns.  The box is
+// laid out in shared memory as the TMA lays it out: rows of 2^c words at a pitch of the
+// swizzle span when the row is narrower than it, and the span's XOR of the 16-byte piece
+// bits with the bits above 128 bytes.  It must fit the 32 KB half of the staging buffer it
+// is read from, and read every staged element into the place the column-blocked layout
+// gives its dyadic output position k: s 2^(a+M) + (k >> c) 2^(a+c) + 2^c r + (k mod 2^c)
+// for row r of signal s.  Every word of the scratch is written once.
+template <int M>
+void tmem_colblock(int a, int c) {
+  using T = TmemCfg<M, 1>;
+  static_assert(T::R == TmemCfg<M, 0>::R && T::JW == TmemCfg<M, 0>::JW, "modes 0 and 1 share the row layout");
+  const int64_t sigs = 2, total = sigs << (a + M);
+  const ColblockView v = colblock_view(total, M, a, c);
+  const uint32_t row_bytes = 4u * v.box[0];
+  const uint32_t span = v.swizzle == CU_TENSOR_MAP_SWIZZLE_128B  ? 128u
+                        : v.swizzle == CU_TENSOR_MAP_SWIZZLE_64B ? 64u
+                        : v.swizzle == CU_TENSOR_MAP_SWIZZLE_32B ? 32u
+                                                                 : 0u;
+  const uint32_t pitch = span > row_bytes ? span : row_bytes;
+  const uint32_t box_bytes = pitch * v.box[1] * v.box[2] * v.box[3] * v.box[4];
+  CHECK(box_bytes <= (4u << (kTmemTB - 1)), "colblock M=%d c=%d: a box takes %u bytes of shared memory, more than %u",
+        M, c, box_bytes, 4u << (kTmemTB - 1));
+  const uint32_t pbits = span == 128u ? 3u : span == 64u ? 2u : span == 32u ? 1u : 0u;  // piece bits the span permutes
+  std::vector<int> hits(static_cast<size_t>(total), 0);
+  for (int q = 0; q < T::R; ++q) {
+    bool ok = true;
+    const std::vector<int64_t> stage = stage_dyadic<M>(q, (1u << (c - 2)) - 1u, &ok);
+    CHECK(ok, "colblock M=%d c=%d: staging", M, c);
+    for (int64_t s = 0; s < sigs; ++s)
+      for (int64_t r = 0; r < (int64_t{1} << a); ++r)
+        for (uint32_t h = 0; h < 2; ++h)
+          for (uint32_t rho = 0; rho < v.box[3]; ++rho)
+            for (uint32_t gl = 0; gl < v.box[2]; ++gl)
+              for (uint32_t w = 0; w < v.box[0]; ++w) {
+                const uint32_t o = (rho * v.box[2] + gl) * pitch + 4u * w;  // byte in the box before the swizzle
+                const uint32_t phys = o ^ (((o >> 7) & ((1u << pbits) - 1u)) << 4);
+                const int64_t label = stage[(h << (kTmemTB - 1)) + phys / 4u];
+                CHECK(label >= 0, "colblock M=%d c=%d: the box reads an unstaged word", M, c);
+                const uint64_t k = bitrev_bits(static_cast<uint32_t>(label), M);
+                const uint64_t x[5] = {w, static_cast<uint64_t>(r), ((64u * q + 32u * h) >> c) + gl, rho,
+                                       static_cast<uint64_t>(s)};
+                for (int i = 0; i < 5; ++i) CHECK(x[i] < v.dims[i], "colblock M=%d c=%d: coordinate %d out of range", M, c, i);
+                const uint64_t addr =
+                    x[0] + (x[1] * v.strides[0] + x[2] * v.strides[1] + x[3] * v.strides[2] + x[4] * v.strides[3]) / 4u;
+                const uint64_t want = (static_cast<uint64_t>(s) << (a + M)) + ((k >> c) << (a + c)) +
+                                      (static_cast<uint64_t>(r) << c) + (k & ((1u << c) - 1u));
+                CHECK(addr == want, "colblock M=%d a=%d c=%d: label %lld stored at %llu, defined at %llu", M, a, c,
+                      static_cast<long long>(label), static_cast<unsigned long long>(addr),
+                      static_cast<unsigned long long>(want));
+                hits[addr]++;
+              }
+  }
+  for (int64_t i = 0; i < total; ++i) CHECK(hits[i] == 1, "colblock M=%d c=%d: word %lld written %d times", M, c,
+                                             static_cast<long long>(i), hits[i]);
+  std::printf("tmem column blocks M=%d a=%d c=%d (%u-byte box rows, swizzle span %u) ok\n", M, a, c, row_bytes, span);
 }
 
 // Tensor-memory kernel, natural order: eight 32-word x 64-row boxes per chunk.
@@ -167,6 +245,10 @@ int main() {
   tmem_dyadic<16>();
   tmem_natural<15>();
   tmem_natural<16>();
+  for (int c = 2; c <= 5; ++c) {
+    tmem_colblock<15>(2, c);
+    tmem_colblock<16>(3, c);
+  }
   std::printf(g_ok ? "ALL OK\n" : "FAILED\n");
   return g_ok ? 0 : 1;
 }

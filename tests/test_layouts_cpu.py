@@ -1,5 +1,6 @@
 """Staging layouts behind the kernels' TMA stores, checked on the CPU with the kernels' own
-constexpr plans: tests/native/layout_check.cu is compiled (host code only) and run."""
+constexpr plans and the two-pass plan's column-blocked tensor view (csrc/colblock.h):
+tests/native/layout_check.cu is compiled (host code only) and run."""
 
 import os
 import shutil
