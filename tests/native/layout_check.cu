@@ -101,6 +101,59 @@ void tmem_dyadic() {
   std::printf("tmem dyadic M=%d ok\n", M);
 }
 
+// Tensor-memory kernel, sequency order: dyadic position p goes to gray^{-1}(p) (the s with
+// s ^ (s >> 1) = p, from a table built from that definition).  The kernel stages run rho's
+// 16-byte group c of chunk q at group C = gray^{-1}(c), complemented when parity(q) differs
+// from the destination run's parity, with its words reordered by parity(c) against that,
+// in box (destination run parity, C / 8) at row (destination run / 2); four TMA stores,
+// each 32 words x 1 x 128 run pairs with the 128-byte swizzle, write the boxes at segment
+// gray^{-1}(q) (complemented for odd destination runs) of the 3-D view {2^(M-8) words,
+// run parity, run pair}.  Every output is written once, with the right value.
+template <int M>
+void tmem_sequency() {
+  using T = TmemCfg<M, 3>;
+  constexpr uint32_t L = M - 8, qmask = (1u << (L - 6)) - 1u;
+  const uint32_t n = 1u << M;
+  std::vector<uint32_t> ginv(n);
+  for (uint32_t x = 0; x < n; ++x) ginv[x ^ (x >> 1)] = x;
+  std::vector<int> out(n, 0);
+  for (int q = 0; q < T::R; ++q) {
+    std::vector<int64_t> stage(1u << kTmemTB, -1);
+    const uint32_t gq = gray_inverse(static_cast<uint32_t>(q)), pq = parity_of(static_cast<uint32_t>(q));
+    for (uint32_t warp = 0; warp < 8; ++warp)
+      for (uint32_t lane = 0; lane < 32; ++lane) {
+        const uint32_t tl = thread_label_host(T::P3, lane, warp);
+        const uint32_t rho = bitrev_bits(tl, 8);
+        const uint32_t dr = gray_inverse(rho), pd = dr & 1u, zr = dr >> 1, zx = zr & 7u, fx = pq ^ pd;
+        for (uint32_t c = 0; c < 16; ++c) {
+          const uint32_t C = gray_inverse(c) ^ (fx ? 15u : 0u);
+          const int order[2][4] = {{0, 1, 3, 2}, {2, 3, 1, 0}};  // value word e' <- group word
+          for (int e = 0; e < 4; ++e) {
+            const int si = T::src(q, 4 * static_cast<int>(c) + order[parity_of(c) ^ fx][e]);
+            const int r = si / T::JW, j = si % T::JW;
+            const uint32_t label = tl | reg_label(T::P3, q * T::JW + j) | (static_cast<uint32_t>(r) << kTmemTB);
+            const uint32_t sm = (pd << (kTmemTB - 2)) + (zr << 5) + ((C >> 3) << (kTmemTB - 1)) + (((C & 7u) ^ zx) << 2) + e;
+            CHECK(stage[sm] < 0, "sequency M=%d q=%d: staged twice at %u", M, q, sm);
+            stage[sm] = label;
+          }
+        }
+      }
+    for (uint32_t pp = 0; pp < 2; ++pp)
+      for (uint32_t h = 0; h < 2; ++h)
+        for (uint32_t zl = 0; zl < 128; ++zl)
+          for (uint32_t x = 0; x < 32; ++x) {
+            const uint32_t sm = (h << (kTmemTB - 1)) + (pp << (kTmemTB - 2)) + zl * 32u + (((x >> 2) ^ (zl & 7u)) << 2) + (x & 3u);
+            const uint32_t xc = 64u * (gq ^ (pp ? qmask : 0u)) + 32u * h + x;  // the view's coordinates
+            const uint32_t pos = ((2u * zl + pp) << L) + xc;
+            CHECK(stage[sm] >= 0, "sequency M=%d: box reads an unstaged word", M);
+            CHECK(pos == ginv[bitrev_bits(static_cast<uint32_t>(stage[sm]), M)], "sequency M=%d: box of pos %u", M, pos);
+            out[pos]++;
+          }
+  }
+  for (uint32_t i = 0; i < n; ++i) CHECK(out[i] == 1, "sequency M=%d: output %u written %d times", M, i, out[i]);
+  std::printf("tmem sequency M=%d ok\n", M);
+}
+
 // Tensor-memory kernel as the first pass of a two-pass split (output mode 1), its chunks
 // written by TMA stores through the column-blocked view `colblock_view` (the plan's own
 // encoding).  The kernel stages with key 2^(c-2) - 1 for blocks of 2^c columns.  The box is
@@ -245,6 +298,8 @@ int main() {
   tmem_dyadic<16>();
   tmem_natural<15>();
   tmem_natural<16>();
+  tmem_sequency<15>();
+  tmem_sequency<16>();
   for (int c = 2; c <= 5; ++c) {
     tmem_colblock<15>(2, c);
     tmem_colblock<16>(3, c);
