@@ -315,10 +315,11 @@ chw_status_t chw_forward_host(chw_plan_t plan, const void* x_host, void* y_host,
  * It launches exactly what chw_forward does for a two-pass plan of the same shape (same
  * split, same kernels, bit-identical results).  No plan object, no cudaMalloc/cudaFree.
  * The first call on a device looks up the array's device address (once per device, with
- * that device current); make that first call before any stream capture.  All calls share
- * the array, which keeps the previous call's contents: calls whose work overlaps on the
- * GPU (different streams, or devices sharing no order) race on it and must be serialised
- * by the caller.  A bounded device wait that gives up latches CHW_ERR_TIMEOUT into the
+ * that device current); make that first call before any stream capture.  Each device has
+ * its own copy of the array, and all calls on a device share it, keeping the previous
+ * call's contents: calls on one device whose work overlaps (different streams with no
+ * order between them) race on it and must be serialised by the caller.  A bounded device
+ * wait that gives up latches CHW_ERR_TIMEOUT into the
  * array's header word, which each call clears first; read it with
  * chw_noalloc_device_status().
  */
