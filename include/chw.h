@@ -15,7 +15,8 @@
  * butterflies on the same operands, so results round exactly as the cascade taken in
  * the paper's stage order does.  Signals of 2^15 and 2^16 elements are held on one SM,
  * their rows in shared memory and the whole signal in the SM's tensor memory (tcgen05),
- * between the row butterflies and the last ones.
+ * between the row butterflies and the last ones; signals of 2^17 on a pair of SMs, half
+ * in each, the last label bit exchanged through L2.
  *
  * Conventions for every call below:
  *   - Pointers named x, y, exp_*, diag are DEVICE pointers unless the name says _host.
@@ -118,7 +119,7 @@ typedef struct chw_plan_info_s {
                                 5 fused 16-bit, 6 row-stack (one CTA, L2-resident rows),
                                 7 tensor memory (one CTA per signal, m = 15, 16),
                                 8 tensor memory over a cluster (m = 17: two SMs hold a
-                                  signal and exchange its last label bit over DSMEM)  */
+                                  signal and exchange its last label bit through L2) */
   int passes;                /* HBM round trips per call                               */
   int row_bits;              /* two-pass: bits transformed in pass 1 (else m)          */
   int cluster;               /* CTAs per cluster in the fused (or first) pass          */
@@ -271,8 +272,11 @@ chw_status_t chw_haar_inverse(chw_plan_t plan, const void* z, void* x, void* str
  * coefficients z (layout above) to Walsh-Hadamard coefficients in dyadic order.  These are
  * stages r = 1..m-1 of Theorem 1; by eq. (4) they act on each Haar scale separately, the
  * level-l details (2^k values, k = m - l) going through H_k and z[0] through 1, so the
- * call runs all scales of all signals as one ragged task set (scales of more than 2^20
- * elements as separate two-pass transforms).  With PER_LEVEL or NONE the result equals
+ * call transforms the scales independently: every scale below 2^14 of every signal in one
+ * tile kernel (the head), the scales 2^14..2^17 as batched launches over strided units
+ * (with the head on branches forked from the caller's stream and joined again), each
+ * larger scale as a two-pass transform; a batch whose total is not a multiple of 32
+ * elements (m < 5) runs as one ragged task set.  With PER_LEVEL or NONE the result equals
  * chw_forward(x) bit for bit when z = chw_haar(x); with END each scale k is scaled once by
  * fp32(2^{-k/2}).  In-place (z == y) allowed.  The plan must have been made with
  * CHW_FLAG_HAAR_WALSH (which builds the task set); otherwise CHW_ERR_INVALID_ARG.
