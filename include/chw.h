@@ -349,8 +349,9 @@ chw_status_t chw_plan_get_info(chw_plan_t plan, chw_plan_info_t* info);
  * Choices are cached per process under (device name, m, floor(log2 batch), dtype, norm,
  * order); a later plan with the same key takes the cached choice (tuned = 2).  When
  * CHW_TUNE_CACHE names a file, it is read on the first autotuned plan and rewritten after
- * each new measurement.  Plans with a single configuration (m <= 13, bf16/fp16, or a flag
- * that fixes the tier) are not timed.
+ * each new measurement.  Plans with a single configuration (m <= 13; m = 15 and 16, where
+ * the tensor-memory tier is the only candidate; m = 30; bf16/fp16; or a flag that fixes
+ * the tier) are not timed.
  *
  * chw_tune_candidates   host only: writes up to `cap` candidates for this shape to `out`
  *                       and returns how many there are (0: nothing to choose).
