@@ -52,6 +52,7 @@ TIERS = {
     5: "fused-16bit",
     6: "row-stack",
     7: "tensor-memory",
+    8: "tensor-memory-pair",
 }
 
 
