@@ -1202,9 +1202,10 @@ chw_status_t chw_plan(chw_plan_t* out, int m, int64_t batch, chw_dtype_t dtype, 
   if (!is_lowp(dtype)) {
     p->haar_ws_bytes = static_cast<size_t>(chw::haar_scratch_words(m, batch)) * 4;
     if (p->haar_ws_bytes > 0 && cudaMalloc(&p->haar_ws, p->haar_ws_bytes) != cudaSuccess) {
+      const size_t bytes = p->haar_ws_bytes;
       cudaGetLastError();
       chw_plan_destroy(p);
-      return fail(CHW_ERR_OOM, "Haar scratch of %zu bytes", p->haar_ws_bytes);
+      return fail(CHW_ERR_OOM, "Haar scratch of %zu bytes", bytes);
     }
   }
   if ((flags & CHW_FLAG_HAAR_WALSH) != 0) {
