@@ -283,15 +283,25 @@ void head_gather(int M) {
 
 int main() {
   for (int M = 0; M <= 14; ++M) head_gather(M);
+  // every single-CTA dyadic shape the library instantiates: rows of m = 0..14 and the
+  // two-pass column tiles of 2^a rows x 32 columns, a = 6..9
   fused_tile_store<0, 0, 13>();
+  fused_tile_store<0, 1, 13>();
+  fused_tile_store<0, 2, 13>();
   fused_tile_store<0, 3, 13>();
+  fused_tile_store<0, 4, 13>();
+  fused_tile_store<0, 5, 13>();
+  fused_tile_store<0, 6, 13>();
   fused_tile_store<0, 7, 13>();
+  fused_tile_store<0, 8, 13>();
+  fused_tile_store<0, 9, 13>();
   fused_tile_store<0, 10, 13>();
   fused_tile_store<0, 11, 13>();
   fused_tile_store<0, 12, 13>();
   fused_tile_store<0, 13, 13>();
   fused_tile_store<0, 14, 14>();
   fused_tile_store<5, 6, 13>();
+  fused_tile_store<5, 7, 13>();
   fused_tile_store<5, 8, 13>();
   fused_tile_store<5, 9, 14>();
   tmem_dyadic<15>();
