@@ -518,6 +518,22 @@ def extra_measurements(chw, torch, dev, steps, warmup, peak):
                 oracle=(lambda: O.wht_ordered(ho, m, order, np.float32, "end"), 2 * ho.nbytes,
                         "2 signals, fp32 cascade stored in order"))
             del xo, yo, po
+    # further shapes with quoted rates: the single-CTA tiers at scale (m = 12, 14), m = 15 in
+    # sequency order, and the longest signals (m = 29, 30: 8- and 4-column blocks between
+    # the two passes); a failure is recorded in its row
+    for m, b, order in ((12, 65536, "dyadic"), (14, 16384, "dyadic"), (15, 8192, "sequency"), (29, 1, "dyadic"),
+                        (30, 1, "dyadic")):
+        try:
+            xo = torch.randn(b, 1 << m, device=dev, generator=g)
+            yo = torch.empty_like(xo)
+            po = chw.chw_plan(m, b, "f32", "end", order=order)
+            info = chw.chw_plan_get_info(po)
+            ms = time_device(lambda: chw.chw_forward(po, xo, yo), k, warmup, 1, st)
+            rec(f"m{m}_b{b}_f32_{order}", 2 * xo.numel() * 4, ms, info.kernels_per_call, tier=int(info.tier),
+                passes=int(info.passes))
+            del xo, yo, po
+        except Exception as e:
+            out[f"m{m}_b{b}_f32_{order}"] = {"failed": repr(e)[:300]}
     # ragged: 10,000 signals with m uniform on 6..20 (seed 5), one graph launch
     from paper_1609_06641_gb300 import workloads as W
 
